@@ -1,0 +1,211 @@
+/*
+ * lqcd.h -- C ABI of the GB300 multi-rhs Wilson(-clover) Dirac operator and batched GMRES.
+ *
+ * Every function returns an lqcd_status (0 = OK, > 0 warning, < 0 error) and never
+ * throws or aborts; lqcd_last_error() gives a thread-local message for the last
+ * failing call on the calling thread. All GPU work is enqueued on the caller's
+ * CUDA stream (`stream` is a cudaStream_t passed as void*, NULL = legacy default
+ * stream); no call synchronises the device except where stated.
+ *
+ * Conventions (the paper's Sec. III-A-1 with the readings stated here):
+ *   dims = {T, Z, Y, X}, every extent even and >= 2; direction mu = 0, 1, 2, 3 is
+ *   t, z, y, x. Site number ((t*Z + z)*Y + y)*X + x (last coordinate fastest).
+ *   V = T*Z*Y*X sites, V/2 per parity; parity of a site = (t+z+y+x) mod 2,
+ *   even = 0. Fermion boundary condition in time is `time_bc` (+1 periodic,
+ *   -1 antiperiodic), space is periodic.
+ *   Gamma matrices in the chiral basis gamma_mu = [[0, P_mu], [P_mu^dag, 0]],
+ *   P_t = 1, P_k = i sigma_k; gamma5 = diag(-1, -1, +1, +1).
+ *   D psi(x) = A(x) psi(x) - sum_mu [ pi^-_mu (x) U_mu(x) psi(x+mu)
+ *                                     + pi^+_mu (x) U_mu(x-mu)^dag psi(x-mu) ],
+ *   pi^+-_mu = (1 +- gamma_mu)/2, A(x) = (4 + m0) 1 - C(x),
+ *   C(x) = (c_sw/32) sum_{mu,nu} gamma_mu gamma_nu (x) (Q_mu,nu(x) - Q_nu,mu(x))
+ *   (clover-leaf sum Q of the four plaquettes in the mu-nu plane at x).
+ *   Odd-even (Sec. III-A-2): the Schur complement on the odd sites,
+ *   S = A_oo - D_oe A_ee^{-1} D_eo.
+ *
+ * Canonical ("user") layouts, complex numbers stored interleaved (re, im):
+ *   gauge field: complex128 [V][4][3][3], U[x][mu][row][col] (row-major 3x3).
+ *   spinor block: complex [nrhs][n_sites][4][3] (spin, colour), rhs outermost;
+ *   n_sites = V for full-lattice vectors, V/2 for one parity (its sites in
+ *   increasing site number).
+ * Packed ("internal") layout: complex [n_sites/S][12][S][nrhs] with component
+ * index 3*spin + colour and the rhs index innermost (Eq. (2)'s rows stored
+ * rhs-fastest), S = lqcd_site_tile(nrhs). Full-lattice packed vectors hold the
+ * even sites first, then the odd sites, each in increasing site number. The
+ * packed layout is what the operator kernels read and write; its byte size is
+ * lqcd_packed_bytes().
+ *
+ * Pointers: unless a parameter says "host or device", pointers are device
+ * pointers that stay owned by the caller. The library owns its copies of the
+ * gauge field, the clover blocks and all workspace, and frees them in
+ * lqcd_free(). Device pointers must be 16-byte aligned.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lqcd_status;
+enum {
+  LQCD_OK = 0,
+  LQCD_NOT_CONVERGED = 1,   /* warning: solve stopped at max_restarts; x holds the last iterate */
+  LQCD_ERR_ARG = -1,        /* invalid argument (null pointer, bad size, odd extent, ...) */
+  LQCD_ERR_OOM = -2,        /* device or pinned-host allocation failed */
+  LQCD_ERR_CUDA = -3,       /* a CUDA runtime call failed; lqcd_last_error() has its text */
+  LQCD_ERR_NONFINITE = -4,  /* NaN or Inf met in a right-hand side or a residual norm */
+  LQCD_ERR_SINGULAR = -5,   /* a 6x6 site block of A(x) has no stable inverse */
+  LQCD_ERR_STATE = -6       /* call out of order (e.g. apply before set_gauge) */
+};
+
+typedef enum {
+  LQCD_C64 = 1,    /* complex64: FP32 storage and arithmetic */
+  LQCD_C128 = 2    /* complex128: FP64 storage and arithmetic */
+} lqcd_dtype;
+
+typedef enum {
+  LQCD_OP_FULL = 0,   /* D on all V sites */
+  LQCD_OP_SCHUR = 1   /* S = A_oo - D_oe A_ee^{-1} D_eo on the V/2 odd sites */
+} lqcd_op;
+
+typedef enum {
+  LQCD_SITES_FULL = 0,
+  LQCD_SITES_EVEN = 1,
+  LQCD_SITES_ODD = 2
+} lqcd_sites;
+
+typedef struct lqcd_ctx_s* lqcd_ctx;
+
+/* Status text ("ok", "invalid argument", ...); static storage, never NULL. */
+const char* lqcd_status_string(lqcd_status s);
+/* Message of the last failing call on this thread ("" if none); valid until the next call. */
+const char* lqcd_last_error(void);
+
+/* Create a lattice context (Sec. III-A-1 lattice and site numbering).
+ * dims: host array {T, Z, Y, X}, each even and >= 2, V <= 2^31 / 12 sites.
+ * time_bc: +1 or -1. *out receives the handle. No GPU work. */
+lqcd_status lqcd_create(const int dims[4], int time_bc, lqcd_ctx* out);
+/* Release every device and host resource of ctx; NULL-safe. Synchronises the device. */
+lqcd_status lqcd_free(lqcd_ctx ctx);
+
+/* Set the gauge field (Sec. III-A-1, U_mu(x) row-major 3x3 per site and direction).
+ * U: host or device, complex128 [V][4][3][3]; read during the call (host: copied
+ * synchronously). Builds the library's packed link copies in FP64 and FP32 with
+ * the time boundary factor folded into U_0 on the last time slice. Invalidates
+ * the site blocks: call lqcd_set_clover() afterwards. */
+lqcd_status lqcd_set_gauge(lqcd_ctx ctx, const void* U, void* stream);
+
+/* Set the bare mass m0 and clover coefficient c_sw and build the site blocks
+ * A(x) = (4 + m0) - C(x) and A(x)^{-1} (Sec. III-A-1 clover term; the inverse
+ * of Sec. III-A-2's odd-even preconditioning) from the current gauge field, in
+ * FP64, then their FP32 copies. c_sw = 0 gives the plain Wilson operator (no
+ * block arrays are read by the kernels then). Synchronises `stream` to read
+ * the singularity flag: LQCD_ERR_SINGULAR if a 6x6 block has a pivot below
+ * 1e-14 times its largest entry. */
+lqcd_status lqcd_set_clover(lqcd_ctx ctx, double m0, double c_sw, void* stream);
+
+/* Copy the site blocks out for inspection: which = 0 gives A(x), 1 gives A(x)^{-1}.
+ * out: device, complex128 [V][12][12] row-major per site, component index
+ * 3*spin + colour, sites in canonical order. */
+lqcd_status lqcd_export_blocks(lqcd_ctx ctx, int which, void* out, void* stream);
+
+/* Site tile S of the packed layout for nrhs right-hand sides (a power of two). */
+int lqcd_site_tile(int nrhs);
+/* Bytes of one packed spinor block for (dtype, sites, nrhs); 0 on bad arguments. */
+size_t lqcd_packed_bytes(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs);
+
+/* Canonical <-> packed conversion of a spinor block (the layout change of
+ * Sec. III-A-2's remark that reordering before and after a solve is cheap).
+ * in/out: device; canonical complex[nrhs][n_sites][4][3] of `dtype`, packed as
+ * described above. For sites = FULL the canonical block lists all V sites in
+ * site order; for EVEN/ODD it lists that parity's V/2 sites. */
+lqcd_status lqcd_pack(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
+                      const void* in, void* out, void* stream);
+lqcd_status lqcd_unpack(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
+                        const void* in, void* out, void* stream);
+
+/* eta = op psi on a block of nrhs right-hand sides (Algorithm 1 with the rhs
+ * loop inside the site loop, Sec. III-A-1 Eq. (1)-(2)), packed layout.
+ * op = FULL: in/out are full-lattice packed blocks (V sites).
+ * op = SCHUR: in/out are odd-site packed blocks (V/2 sites); the intermediate
+ * A_ee^{-1} D_eo psi lives in library workspace (allocated on first use for
+ * this (dtype, nrhs), then reused). in and out must not overlap.
+ * nrhs: 1..256. Requires set_gauge and set_clover. */
+lqcd_status lqcd_apply_packed(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs,
+                              const void* in, void* out, void* stream);
+
+/* Same operator on canonical-layout device blocks: packs, applies, unpacks
+ * through library workspace. */
+lqcd_status lqcd_apply(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs,
+                       const void* in, void* out, void* stream);
+
+/* Odd-even source preparation and solution reconstruction (Sec. III-A-2),
+ * packed layout, full-lattice blocks hold even then odd sites:
+ *   prepare:     bhat_o = b_o - D_oe A_ee^{-1} b_e          (b full, bhat_o odd)
+ *   reconstruct: x = (A_ee^{-1} (b_e - D_eo x_o), x_o)      (b full, x_o odd, x full) */
+lqcd_status lqcd_schur_prepare(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
+                               const void* b, void* bhat_o, void* stream);
+lqcd_status lqcd_schur_reconstruct(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
+                                   const void* b, const void* x_o, void* x, void* stream);
+
+/* One block Gram-Schmidt step of the Arnoldi process (Algorithm 2, "one step of
+ * Arnoldi"), per rhs: h_i = <v_i, w> for the nvec basis vectors, w <- w - sum_i h_i v_i,
+ * repeated once more when reorth != 0 (CGS2; h accumulates both passes), then
+ * h_norm = ||w||. basis: device, nvec packed blocks back to back (each
+ * lqcd_packed_bytes(dtype, sites, nrhs) bytes); w: device packed block, updated
+ * in place. h: device, complex128 [nvec][nrhs]; hnorm: device, double [nrhs].
+ * nvec: 1..129. Dot products accumulate per thread in the vector precision and
+ * across threads in FP64, in a fixed order (deterministic). */
+lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
+                               int nvec, const void* basis, void* w, void* h, void* hnorm,
+                               int reorth, void* stream);
+
+typedef struct {
+  int op;             /* LQCD_OP_FULL: GMRES on D; LQCD_OP_SCHUR: on S, x_e reconstructed */
+  int precision;      /* LQCD_C128: FP64 Arnoldi; LQCD_C64: FP32 operator and Arnoldi
+                         inside FP64 restarts (iterative refinement) */
+  int restart_len;    /* m, 1..64 */
+  int max_restarts;   /* >= 1 */
+  double tol;         /* stop when ||b - D x|| <= tol ||b|| (true residual, per rhs) */
+  double inner_tol;   /* cycle stops when its Arnoldi estimate <= inner_tol * ||r_restart||
+                         (0: default 1e-5 for C64, none for C128); never below tol ||b|| */
+  int x0_given;       /* 1: x holds the initial guess; 0: start from x = 0 */
+  int use_graph;      /* 1: replay each Arnoldi cycle as a captured CUDA graph */
+  int reorth;         /* 1: CGS2 (default); 0: one classical Gram-Schmidt pass */
+  int profile;        /* 1: time operator and Gram-Schmidt launches with CUDA events
+                         (use_graph is then ignored) */
+} lqcd_solve_params;
+
+typedef struct {
+  int status;            /* LQCD_OK or LQCD_NOT_CONVERGED */
+  int restarts;          /* FP64 restarts (true-residual evaluations after the first) */
+  int iterations;        /* Arnoldi steps, max over rhs */
+  double seconds;        /* host wall time of the call */
+  double relres_max;     /* max over rhs of the final ||b - D x|| / ||b|| (full operator) */
+  /* profile = 1 only (else 0): summed CUDA-event time and count of launches */
+  double op_ms; int op_launches;       /* inner-precision operator applies */
+  double ortho_ms; int ortho_launches; /* Gram-Schmidt dot/update passes */
+  /* optional per-rhs outputs (host arrays of nrhs entries, may be NULL) */
+  int* iters_per_rhs;
+  double* relres_per_rhs;
+} lqcd_solve_stats;
+
+/* Batched restarted GMRES (Algorithm 2), each rhs independent, optionally on the
+ * odd-even Schur system (Sec. III-A-2). b, x: host or device (detected),
+ * canonical complex128 [nrhs][V][4][3]; x is overwritten with the solution
+ * (and read as the initial guess when x0_given). The true residual is
+ * recomputed in FP64 at every restart, each rhs retires once it meets tol,
+ * and the final full-operator residual is reported in stats. Synchronises
+ * `stream` once per restart. Returns LQCD_NOT_CONVERGED if max_restarts is
+ * reached, LQCD_ERR_NONFINITE if b or a residual norm is not finite.
+ * stats: host, may be NULL. nrhs: 1..64. */
+lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* params, int nrhs,
+                       const void* b, void* x, lqcd_solve_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */
