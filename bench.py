@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: multi-rhs Wilson-clover Dirac operator and batched GMRES on one GB300.
+
+One "step" is one pass of the whole path over one batch of rhs: upload-free
+gauge-field packing (set_gauge from the device copy), clover build and inversion
+(set_clover), and an odd-even batched GMRES(32) solve to a 1e-10 true relative
+residual with the FP32 operator and Arnoldi process inside FP64 restarts (the
+solve's last step applies the full FP64 operator to report the final residual).
+
+Workloads (synthetic, seeded; see the design doc for the recipe):
+  solve        16^3 x 32, Wilson-clover c_sw = 1, U = exp(i 0.3 H), m0 = -0.2,
+               nrhs = 16 Gaussian sources (the operator-sweep lattice)   [default]
+  solve-large  32^3 x 64, U = exp(i 0.25 H), m0 = -0.3, nrhs = 12
+
+value = sites x rhs solved per second, summed over ranks (each rank solves its
+own batch: weak scaling, no communication). The JSON line also reports the
+operator sweep (GB/s against the HBM roofline), the FP64-vs-mixed GMRES
+comparison, the roofline of the dominant kernel measured with CUDA events inside
+the timed steps, the CPU oracle baseline and an end-to-end number through the
+C ABI with host buffers.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "multi-rhs Dslash GB/s & site·rhs/s vs HBM roofline; GMRES time-to-1e-10, mixed vs FP64"
+
+WORKLOADS = {
+    "solve": dict(name="eo-gmres32-mixed 16^3x32 clover nrhs=16", dims=(32, 16, 16, 16), eps=0.3, m0=-0.2,
+                  c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, restart=32, tol=1e-10),
+    "solve-large": dict(name="eo-gmres32-mixed 32^3x64 clover nrhs=12", dims=(64, 32, 32, 32), eps=0.25, m0=-0.3,
+                        c_sw=1.0, nrhs=12, gauge_seed=2000, rhs_seed=2001, restart=32, tol=1e-10),
+}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+
+def oracle_sample(w, iters: int):
+    """Time the FP64 numpy oracle's odd-even GMRES for `iters` Arnoldi steps on one rhs."""
+    import numpy as np
+    import oracle
+    import synthetic as syn
+    U = syn.gauge_field(w["dims"], "exp", w["eps"], seed=w["gauge_seed"])
+    b = syn.gaussian_spinors(w["dims"], 1, w["rhs_seed"])
+    t0 = time.perf_counter()
+    A, Ainv = oracle.diag_blocks(U, w["m0"], w["c_sw"])
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.solve_eo(U, A, Ainv, b, tol=1e-30, m=iters, max_restarts=1)
+    t_cycle = time.perf_counter() - t0
+    del np
+    return t_setup, t_cycle
+
+
+def cpu_threads():
+    try:
+        import numpy as np  # noqa: F401
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return 1
+
+
+def run_reference(args, w):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    V = w["dims"][0] * w["dims"][1] * w["dims"][2] * w["dims"][3]
+    # projected time to solution of one rhs: per-iteration oracle cost x the GPU solve's
+    # iteration count for this workload (fixed number recorded from the GPU run)
+    its = args.ref_iterations
+    k = args.ref_sample_iters
+    for _ in range(args.warmup):
+        oracle_sample(w, k)
+    times = []
+    for _ in range(args.steps):
+        ts, tc = oracle_sample(w, k)
+        times.append(ts + tc * its / k)
+    t = statistics.mean(times)
+    value = V * 1 / t
+    sample = (f"oracle odd-even GMRES, 1 rhs, {k} Arnoldi steps + set-up per step, projected to {its} "
+              f"iterations (the GPU solve's count)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site·rhs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": w["name"]},
+            "cpu_baseline": {"value": value, "unit": "site·rhs/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "site·rhs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def dslash_point(lat, lq, torch, dims, nrhs, dtype, op, reps, flush):
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    sites = lq.SITES_FULL if op == lq.OP_FULL else lq.SITES_ODD
+    pin = lat.packed_empty(dtype, sites, nrhs)
+    pout = lat.packed_empty(dtype, sites, nrhs)
+    g = torch.Generator(device="cuda").manual_seed(nrhs)
+    pin.copy_(torch.randn(pin.shape, dtype=pin.dtype, device="cuda", generator=g))
+    for _ in range(3):
+        lat.apply_packed(op, nrhs, pin, pout)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        lat.apply_packed(op, nrhs, pin, pout)
+        e1.record(s)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.median(times)
+    sz = 8 if dtype == lq.C128 else 4
+    if op == lq.OP_FULL:
+        nbytes = V * (48 * nrhs + 144) * sz
+        units = V * nrhs
+    else:
+        nbytes = (V // 2) * (120 * nrhs + 432) * sz
+        units = (V // 2) * nrhs
+    return t, nbytes, units
+
+
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2601_05816_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    import paper_2601_05816_gb300 as lq
+    import synthetic as syn
+    lq.load()
+    dims, nrhs = w["dims"], w["nrhs"]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U = syn.gauge_field(dims, "exp", w["eps"], seed=w["gauge_seed"])
+    b = syn.gaussian_spinors(dims, nrhs, w["rhs_seed"] + 7919 * rank)
+    U_d = torch.from_numpy(U).cuda()
+    b_d = torch.from_numpy(b).cuda()
+    x_d = torch.zeros_like(b_d)
+    lat = lq.Lattice(dims, time_bc=-1)
+    peak, peak_kind = measured_peaks()
+    solve_kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=w["restart"], tol=w["tol"], max_restarts=500,
+                    use_graph=True, profile=True)
+
+    def step():
+        lat.set_gauge(U_d)
+        lat.set_clover(w["m0"], w["c_sw"])
+        x_d.zero_()
+        return lat.solve(b_d, x_d, nrhs, **solve_kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    results = []
+    s = torch.cuda.current_stream()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            results.append(step())
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(world)
+    t_local = e0.elapsed_time(e1) * 1e-3
+    t = allreduce_max(world, t_local)
+    value = world * V * nrhs * args.steps / t
+    for r in results:
+        if r.status != lq.OK or r.relres_max > w["tol"]:
+            raise SystemExit(f"solve did not converge: {r}")
+    clocks = clk.summary()
+
+    # dominant kernel within the timed steps (profiled with CUDA events on the launching stream)
+    op_ms = sum(r.op_ms for r in results)
+    gs_ms = sum(r.ortho_ms for r in results)
+    if gs_ms >= op_ms:
+        dom = dict(kernel="gs_pass (CGS2 step: 3 fused passes)", ms=gs_ms, n=sum(r.ortho_launches for r in results),
+                   bytes=sum(r.ortho_bytes for r in results))
+    else:
+        dom = dict(kernel="dslash (Schur apply: passes A + B)", ms=op_ms, n=sum(r.op_launches for r in results),
+                   bytes=sum(r.op_bytes for r in results))
+    achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "launches": dom["n"], "avg_launch_ms": dom["ms"] / max(dom["n"], 1),
+                "bytes_per_launch": dom["bytes"] / max(dom["n"], 1),
+                "share_of_step": (dom["ms"] * 1e-3) / t_local,
+                "op_ms": op_ms, "ortho_ms": gs_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "site·rhs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32 inner / fp64 refinement", "data": "synthetic",
+            "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in dims[::-1]), "nrhs": nrhs,
+                       "gauge": f"exp(i*{w['eps']}*H)", "m0": w["m0"], "c_sw": w["c_sw"],
+                       "solver": f"odd-even GMRES({w['restart']}) FP32 inside FP64 restarts, tol {w['tol']}",
+                       "parallelism": f"rhs batches, {world} independent rank(s)",
+                       "l2": "working set (basis 33 x %.0f MB) far above the 129 MB L2" %
+                             ((V // 2) * 12 * nrhs * 8 / 1e6)},
+            "roofline": roofline, "clocks": clocks,
+            "solve": {"iterations": [r.iterations for r in results], "restarts": [r.restarts for r in results],
+                      "relres_max": max(r.relres_max for r in results),
+                      "seconds_host": [r.seconds for r in results]},
+            "gpu_launches": int(sum(r.kernel_launches for r in results) + args.steps * 5)}
+
+    if rank == 0 and not args.skip_extras:
+        # operator sweep (dslash GB/s vs HBM roofline), L2 flushed between applies
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        lat.set_gauge(U_d)
+        lat.set_clover(w["m0"], w["c_sw"])
+        sweep = []
+        nr_list = [int(v) for v in args.sweep.split(",")] if args.sweep else [1, 4, 16, 64]
+        for nr in nr_list:
+            for dt in (lq.C64, lq.C128):
+                for op in (lq.OP_SCHUR, lq.OP_FULL):
+                    tt, nb, units = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
+                    sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
+                                  "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
+                                  "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
+                                  "site_rhs_per_s": units / tt})
+        del flush
+        line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48b+144)s/site, "
+                          "schur (120b+432)s/odd site", "l2_flush": "512 MB memset between applies",
+                          "points": sweep}
+        # FP64 plain GPU solve vs the mixed solve of the timed steps
+        torch.cuda.synchronize()
+        x_d.zero_()
+        t0 = time.perf_counter()
+        r64 = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=lq.C128, restart_len=w["restart"], tol=w["tol"],
+                        max_restarts=500, use_graph=True)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        mixed_s = statistics.mean(r.seconds for r in results)
+        line["gmres"] = {"fp64_s": t64, "mixed_s": mixed_s, "speedup": t64 / mixed_s,
+                         "fp64_iterations": r64.iterations, "mixed_iterations": results[-1].iterations,
+                         "fp64_relres": r64.relres_max, "mixed_relres": results[-1].relres_max,
+                         "note": "host wall time of one synchronised solve (step includes set_gauge/set_clover)"}
+        # end to end through the C ABI with pinned host buffers
+        U_h = torch.from_numpy(U).pin_memory()
+        b_h = torch.from_numpy(b).pin_memory()
+        x_h = torch.zeros_like(b_h).pin_memory()
+        lat.set_gauge(U_h.numpy())
+        lat.set_clover(w["m0"], w["c_sw"])
+        lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            lat.set_gauge(U_h.numpy())
+            lat.set_clover(w["m0"], w["c_sw"])
+            re = lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / e2e_steps
+        line["e2e"] = {"value": V * nrhs / te, "unit": "site·rhs/s", "h2d_bytes_per_step": U.nbytes + b.nbytes,
+                       "d2h_bytes_per_step": b.nbytes, "relres_max": re.relres_max,
+                       "api": "lqcd_set_gauge + lqcd_set_clover + lqcd_solve with pinned host pointers"}
+        # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+        if world == 1 and not args.skip_cpu:
+            its_gpu = statistics.mean(statistics.mean(results[-1].iters_per_rhs) for _ in range(1))
+            k = args.ref_sample_iters
+            ts, tc = oracle_sample(w, k)
+            t_proj = ts + tc * its_gpu / k
+            line["cpu_baseline"] = {"value": V / t_proj, "unit": "site·rhs/s", "cores": cpu_threads(),
+                                    "kind": "oracle",
+                                    "sample": f"numpy FP64 oracle odd-even GMRES on 1 rhs of the same workload: "
+                                              f"set-up {ts:.1f} s + {k} Arnoldi steps {tc:.1f} s, projected to "
+                                              f"{its_gpu:.0f} iterations (the GPU solve's mean per rhs)"}
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="solve", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweep", default="", help="comma-separated nrhs list for the operator sweep")
+    ap.add_argument("--dslash-reps", type=int, default=20)
+    ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ref-sample-iters", type=int, default=4)
+    ap.add_argument("--ref-iterations", type=int, default=300)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -30,7 +30,7 @@
  *   increasing site number).
  * Packed ("internal") layout: complex [n_sites/S][12][S][nrhs] with component
  * index 3*spin + colour and the rhs index innermost (Eq. (2)'s rows stored
- * rhs-fastest), S = lqcd_site_tile(nrhs). Full-lattice packed vectors hold the
+ * rhs-fastest), S = lqcd_site_tile(ctx, nrhs). Full-lattice packed vectors hold the
  * even sites first, then the odd sites, each in increasing site number. The
  * packed layout is what the operator kernels read and write; its byte size is
  * lqcd_packed_bytes().
@@ -112,8 +112,10 @@ lqcd_status lqcd_set_clover(lqcd_ctx ctx, double m0, double c_sw, void* stream);
  * 3*spin + colour, sites in canonical order. */
 lqcd_status lqcd_export_blocks(lqcd_ctx ctx, int which, void* out, void* stream);
 
-/* Site tile S of the packed layout for nrhs right-hand sides (a power of two). */
-int lqcd_site_tile(int nrhs);
+/* Site tile S of the packed layout for nrhs right-hand sides on this lattice: the
+ * smallest power of two with S * nrhs >= 16, capped at 16 and at the largest
+ * power of two dividing V/2. 0 on bad arguments. */
+int lqcd_site_tile(lqcd_ctx ctx, int nrhs);
 /* Bytes of one packed spinor block for (dtype, sites, nrhs); 0 on bad arguments. */
 size_t lqcd_packed_bytes(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs);
 
@@ -185,9 +187,12 @@ typedef struct {
   int iterations;        /* Arnoldi steps, max over rhs */
   double seconds;        /* host wall time of the call */
   double relres_max;     /* max over rhs of the final ||b - D x|| / ||b|| (full operator) */
-  /* profile = 1 only (else 0): summed CUDA-event time and count of launches */
-  double op_ms; int op_launches;       /* inner-precision operator applies */
-  double ortho_ms; int ortho_launches; /* Gram-Schmidt dot/update passes */
+  /* profile = 1 only (else 0): summed CUDA-event time, count and algorithmic bytes
+   * (bytes the operation must move at least once, see the byte model in the
+   * documentation) of the Arnoldi steps that ran */
+  double op_ms; int op_launches; double op_bytes;          /* inner-precision operator applies */
+  double ortho_ms; int ortho_launches; double ortho_bytes; /* Gram-Schmidt steps (all passes) */
+  long long kernel_launches;  /* CUDA kernels this call launched, graph nodes included */
   /* optional per-rhs outputs (host arrays of nrhs entries, may be NULL) */
   int* iters_per_rhs;
   double* relres_per_rhs;

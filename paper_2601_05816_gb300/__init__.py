@@ -1,0 +1,246 @@
+"""Python binding of liblqcd.so: the GB300 multi-rhs Wilson(-clover) operator and batched GMRES.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in ``include/lqcd.h``. PyTorch provides device
+memory and the current CUDA stream; tensors are passed by ``data_ptr()``.
+There is no CPU fallback: if the library is missing or cannot be loaded the
+calls raise ``LqcdError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblqcd.so")
+
+# status codes and enums (include/lqcd.h)
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_SINGULAR, ERR_STATE = -1, -2, -3, -4, -5, -6
+C64, C128 = 1, 2
+OP_FULL, OP_SCHUR = 0, 1
+SITES_FULL, SITES_EVEN, SITES_ODD = 0, 1, 2
+
+_lib = None
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int), ("precision", ctypes.c_int), ("restart_len", ctypes.c_int),
+        ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+        ("x0_given", ctypes.c_int), ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int),
+        ("profile", ctypes.c_int),
+    ]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("restarts", ctypes.c_int), ("iterations", ctypes.c_int),
+        ("seconds", ctypes.c_double), ("relres_max", ctypes.c_double),
+        ("op_ms", ctypes.c_double), ("op_launches", ctypes.c_int), ("op_bytes", ctypes.c_double),
+        ("ortho_ms", ctypes.c_double), ("ortho_launches", ctypes.c_int), ("ortho_bytes", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
+        ("iters_per_rhs", ctypes.POINTER(ctypes.c_int)),
+        ("relres_per_rhs", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_VP, _I, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_SIGS = {
+    "lqcd_status_string": (ctypes.c_char_p, [_I]),
+    "lqcd_last_error": (ctypes.c_char_p, []),
+    "lqcd_create": (_I, [ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(_VP)]),
+    "lqcd_free": (_I, [_VP]),
+    "lqcd_set_gauge": (_I, [_VP, _VP, _VP]),
+    "lqcd_set_clover": (_I, [_VP, _D, _D, _VP]),
+    "lqcd_export_blocks": (_I, [_VP, _I, _VP, _VP]),
+    "lqcd_site_tile": (_I, [_VP, _I]),
+    "lqcd_packed_bytes": (_SZ, [_VP, _I, _I, _I]),
+    "lqcd_pack": (_I, [_VP, _I, _I, _I, _VP, _VP, _VP]),
+    "lqcd_unpack": (_I, [_VP, _I, _I, _I, _VP, _VP, _VP]),
+    "lqcd_apply_packed": (_I, [_VP, _I, _I, _I, _VP, _VP, _VP]),
+    "lqcd_apply": (_I, [_VP, _I, _I, _I, _VP, _VP, _VP]),
+    "lqcd_schur_prepare": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "lqcd_schur_reconstruct": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP]),
+    "lqcd_orthogonalise": (_I, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
+    "lqcd_solve": (_I, [_VP, ctypes.POINTER(SolveParams), _I, _VP, _VP, ctypes.POINTER(SolveStats), _VP]),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblqcd.so (built by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LqcdError(ERR_STATE, f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        msg = load().lqcd_last_error().decode(errors="replace")
+        raise LqcdError(status, f"{what}: {msg}")
+    return status
+
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _ptr(t) -> int:
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise LqcdError(ERR_ARG, "tensor must be contiguous")
+        return int(t.data_ptr())
+    import numpy as np
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise LqcdError(ERR_ARG, "array must be C-contiguous")
+        return int(t.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(t)}")
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise LqcdError(ERR_ARG, f"unsupported dtype {t.dtype}")
+
+
+@dataclass
+class SolveResult:
+    status: int
+    restarts: int
+    iterations: int
+    seconds: float
+    relres_max: float
+    op_ms: float
+    op_launches: int
+    op_bytes: float
+    ortho_ms: float
+    ortho_launches: int
+    ortho_bytes: float
+    kernel_launches: int
+    iters_per_rhs: list
+    relres_per_rhs: list
+
+
+class Lattice:
+    """A lattice context: gauge field, clover blocks and library workspace.
+
+    dims = (T, Z, Y, X), all even; time_bc = -1 (antiperiodic) or +1.
+    """
+
+    def __init__(self, dims, time_bc: int = -1):
+        lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        arr = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib.lqcd_create(arr, int(time_bc), ctypes.byref(h)), "lqcd_create")
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.lqcd_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_gauge(self, U, stream=None):
+        """U: complex128 [V][4][3][3] (any shape with that memory layout), torch CUDA tensor or numpy."""
+        _check(self._lib.lqcd_set_gauge(self._h, _ptr(U), _stream(stream)), "lqcd_set_gauge")
+
+    def set_clover(self, m0: float, c_sw: float, stream=None):
+        _check(self._lib.lqcd_set_clover(self._h, float(m0), float(c_sw), _stream(stream)), "lqcd_set_clover")
+
+    def export_blocks(self, which: int, out, stream=None):
+        _check(self._lib.lqcd_export_blocks(self._h, int(which), _ptr(out), _stream(stream)),
+               "lqcd_export_blocks")
+
+    def site_tile(self, nrhs: int) -> int:
+        return int(self._lib.lqcd_site_tile(self._h, int(nrhs)))
+
+    def packed_bytes(self, dtype: int, sites: int, nrhs: int) -> int:
+        return int(self._lib.lqcd_packed_bytes(self._h, int(dtype), int(sites), int(nrhs)))
+
+    def packed_empty(self, dtype: int, sites: int, nrhs: int):
+        import torch
+        n = self.packed_bytes(dtype, sites, nrhs) // (16 if dtype == C128 else 8)
+        return torch.empty(n, dtype=torch.complex128 if dtype == C128 else torch.complex64, device="cuda")
+
+    def pack(self, sites: int, nrhs: int, src, dst, stream=None):
+        _check(self._lib.lqcd_pack(self._h, _dtype_code(src), int(sites), int(nrhs), _ptr(src), _ptr(dst),
+                                   _stream(stream)), "lqcd_pack")
+
+    def unpack(self, sites: int, nrhs: int, src, dst, stream=None):
+        _check(self._lib.lqcd_unpack(self._h, _dtype_code(src), int(sites), int(nrhs), _ptr(src), _ptr(dst),
+                                     _stream(stream)), "lqcd_unpack")
+
+    def apply_packed(self, op: int, nrhs: int, src, dst, stream=None):
+        _check(self._lib.lqcd_apply_packed(self._h, int(op), _dtype_code(src), int(nrhs), _ptr(src), _ptr(dst),
+                                           _stream(stream)), "lqcd_apply_packed")
+
+    def apply(self, op: int, nrhs: int, src, dst, stream=None):
+        _check(self._lib.lqcd_apply(self._h, int(op), _dtype_code(src), int(nrhs), _ptr(src), _ptr(dst),
+                                    _stream(stream)), "lqcd_apply")
+
+    def schur_prepare(self, nrhs: int, b_full, bhat_o, stream=None):
+        _check(self._lib.lqcd_schur_prepare(self._h, _dtype_code(b_full), int(nrhs), _ptr(b_full), _ptr(bhat_o),
+                                            _stream(stream)), "lqcd_schur_prepare")
+
+    def schur_reconstruct(self, nrhs: int, b_full, x_o, x_full, stream=None):
+        _check(self._lib.lqcd_schur_reconstruct(self._h, _dtype_code(b_full), int(nrhs), _ptr(b_full), _ptr(x_o),
+                                                _ptr(x_full), _stream(stream)), "lqcd_schur_reconstruct")
+
+    def orthogonalise(self, sites: int, nrhs: int, nvec: int, basis, w, h, hnorm, reorth: bool = True,
+                      stream=None):
+        _check(self._lib.lqcd_orthogonalise(self._h, _dtype_code(w), int(sites), int(nrhs), int(nvec),
+                                            _ptr(basis), _ptr(w), _ptr(h), _ptr(hnorm), int(bool(reorth)),
+                                            _stream(stream)), "lqcd_orthogonalise")
+
+    def solve(self, b, x, nrhs: int, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
+              max_restarts: int = 200, tol: float = 1e-10, inner_tol: float = 0.0, x0_given: bool = False,
+              use_graph: bool = True, reorth: bool = True, profile: bool = False, stream=None) -> SolveResult:
+        """Batched GMRES on D x = b; b and x complex128 canonical [nrhs][V][4][3], host (numpy) or device."""
+        p = SolveParams(op, precision, restart_len, max_restarts, tol, inner_tol, int(x0_given), int(use_graph),
+                        int(reorth), int(profile))
+        its = (ctypes.c_int * nrhs)()
+        rel = (ctypes.c_double * nrhs)()
+        st = SolveStats()
+        st.iters_per_rhs = ctypes.cast(its, ctypes.POINTER(ctypes.c_int))
+        st.relres_per_rhs = ctypes.cast(rel, ctypes.POINTER(ctypes.c_double))
+        status = _check(self._lib.lqcd_solve(self._h, ctypes.byref(p), int(nrhs), _ptr(b), _ptr(x),
+                                             ctypes.byref(st), _stream(stream)), "lqcd_solve")
+        return SolveResult(status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
+                           st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
+                           st.kernel_launches, list(its), list(rel))

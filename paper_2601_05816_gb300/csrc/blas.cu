@@ -1,0 +1,376 @@
+// Multi-rhs vector kernels of the batched GMRES (Algorithm 2) on packed blocks.
+//
+// A packed block of n complex numbers holds nrhs right-hand sides interleaved
+// with the rhs index innermost, so element e belongs to rhs e % nrhs. Every
+// streaming kernel runs a thread count that is a multiple of nrhs and strides
+// by a multiple of nrhs, so each thread owns one rhs and keeps per-rhs partial
+// sums in registers: the lane separation of the paper's Layout-2 dot product
+// (Sec. V-B, Fig. 7) is delayed to the very end, where a block reduction in
+// FP64 and a fixed-order cross-block sum (reduce_partials) produce one value
+// per (vector, rhs). The summation order depends only on the launch shape, so
+// results are bitwise reproducible run to run.
+#include "kernels.h"
+
+namespace lqcd {
+
+BlasPlan blas_plan(int64_t n, int nrhs, int num_sms) {
+  BlasPlan p;
+  p.nrhs = nrhs;
+  p.threads = nrhs * (256 / nrhs);
+  int64_t want = (n + p.threads - 1) / p.threads;
+  int64_t cap = 2 * (int64_t)num_sms;
+  p.blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  return p;
+}
+
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<double2> { using T = double; };
+
+// Block reduction of per-thread values (one per slot) into partials[blockIdx][slot][rhs].
+template <int NS>
+__device__ __forceinline__ void block_reduce_slots(const double (&vr)[NS], const double (&vi)[NS],
+                                                   int nslots, int nrhs, double2* partials) {
+  __shared__ double2 red[256];
+  const int tid = threadIdx.x;
+  const int per = blockDim.x / nrhs;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (s >= nslots) break;
+    red[tid] = make_double2(vr[s], vi[s]);
+    __syncthreads();
+    if (tid < nrhs) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int q = 0; q < per; ++q) {
+        const double2 v = red[tid + q * nrhs];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      partials[((int64_t)blockIdx.x * nslots + s) * nrhs + tid] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Fixed-order sum of partials[blk][q] over blk for q < nq; one warp per q.
+__global__ void reduce_partials_kernel(int nblk, int nq, const double2* __restrict__ partials,
+                                       double2* __restrict__ out, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nq) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    const double2 v = partials[(int64_t)b * nq + warp];
+    sx += v.x;
+    sy += v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+  }
+  if (lane == 0) out[warp] = make_double2(sx, sy);
+}
+
+static cudaError_t launch_reduce(int nblk, int nq, const void* partials, void* out, const int* skip,
+                                 cudaStream_t stream) {
+  const int threads = 256;
+  const int blocks = (nq * 32 + threads - 1) / threads;
+  reduce_partials_kernel<<<blocks, threads, 0, stream>>>(nblk, nq, (const double2*)partials,
+                                                          (double2*)out, skip);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Gram-Schmidt pass
+
+template <typename C, int NVB, bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(256)
+gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64_t vstride,
+               C* __restrict__ w, const double2* __restrict__ coef, double2* __restrict__ partials,
+               const int* skip) {
+  using Real = typename RealOf<C>::T;
+  if (skip != nullptr && *skip != 0) return;
+  const int tid = threadIdx.x;
+  const int r = tid % nrhs;
+  Real cr[NVB], ci[NVB], ar[NVB], ai[NVB];
+#pragma unroll
+  for (int i = 0; i < NVB; ++i) {
+    ar[i] = 0; ai[i] = 0; cr[i] = 0; ci[i] = 0;
+    if (UPDATE && i < nvec) {
+      const double2 c = coef[(int64_t)i * nrhs + r];
+      cr[i] = (Real)c.x;
+      ci[i] = (Real)c.y;
+    }
+  }
+  Real nn = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < n; e += stride) {
+    C wv = w[e];
+    if (UPDATE) {
+      C v[NVB];
+#pragma unroll
+      for (int i = 0; i < NVB; ++i)
+        if (i < nvec) v[i] = __ldg(basis + i * vstride + e);
+#pragma unroll
+      for (int i = 0; i < NVB; ++i) {
+        if (i < nvec) {
+          wv.x -= cr[i] * v[i].x - ci[i] * v[i].y;
+          wv.y -= cr[i] * v[i].y + ci[i] * v[i].x;
+        }
+      }
+      w[e] = wv;
+      if (DOTS) {
+#pragma unroll
+        for (int i = 0; i < NVB; ++i) {
+          if (i < nvec) {
+            ar[i] += v[i].x * wv.x + v[i].y * wv.y;
+            ai[i] += v[i].x * wv.y - v[i].y * wv.x;
+          }
+        }
+      }
+    } else if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < NVB; ++i) {
+        if (i < nvec) {
+          const C v = __ldg(basis + i * vstride + e);
+          ar[i] += v.x * wv.x + v.y * wv.y;
+          ai[i] += v.x * wv.y - v.y * wv.x;
+        }
+      }
+    }
+    if (NORM) nn += wv.x * wv.x + wv.y * wv.y;
+  }
+  double vr[NVB + 1], vi[NVB + 1];
+#pragma unroll
+  for (int i = 0; i < NVB + 1; ++i) { vr[i] = 0.0; vi[i] = 0.0; }
+#pragma unroll
+  for (int i = 0; i < NVB; ++i)
+    if (i < nvec) { vr[i] = DOTS ? (double)ar[i] : 0.0; vi[i] = DOTS ? (double)ai[i] : 0.0; }
+  // norm goes to slot nvec
+#pragma unroll
+  for (int i = 0; i < NVB + 1; ++i)
+    if (i == nvec) { vr[i] = NORM ? (double)nn : 0.0; vi[i] = 0.0; }
+  block_reduce_slots<NVB + 1>(vr, vi, nvec + 1, nrhs, partials);
+}
+
+template <typename C, int NVB>
+static void gs_dispatch(const BlasPlan& p, int64_t n, int nvec, const void* basis, int64_t vstride,
+                        void* w, const void* coef, bool update, bool dots, bool norm, void* partials,
+                        const int* skip, cudaStream_t stream) {
+  const C* b = (const C*)basis;
+  C* wp = (C*)w;
+  const double2* cf = (const double2*)coef;
+  double2* pa = (double2*)partials;
+#define GS_LAUNCH(U, D, N) \
+  gs_pass_kernel<C, NVB, U, D, N><<<p.blocks, p.threads, 0, stream>>>(n, p.nrhs, nvec, b, vstride, wp, cf, pa, skip)
+  if (update) {
+    if (dots) { if (norm) GS_LAUNCH(true, true, true); else GS_LAUNCH(true, true, false); }
+    else { if (norm) GS_LAUNCH(true, false, true); else GS_LAUNCH(true, false, false); }
+  } else {
+    if (dots) { if (norm) GS_LAUNCH(false, true, true); else GS_LAUNCH(false, true, false); }
+    else GS_LAUNCH(false, false, true);
+  }
+#undef GS_LAUNCH
+}
+
+cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
+                           int64_t vstride, void* w, const void* coef, bool update, bool dots,
+                           bool norm, void* partials, void* out, const int* skip,
+                           cudaStream_t stream) {
+  if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
+#define GS_NVB(NV)                                                                                \
+  if (f64) gs_dispatch<double2, NV>(plan, n, nvec, basis, vstride, w, coef, update, dots, norm,   \
+                                    partials, skip, stream);                                      \
+  else gs_dispatch<float2, NV>(plan, n, nvec, basis, vstride, w, coef, update, dots, norm,        \
+                               partials, skip, stream);
+  if (nvec <= 4) { GS_NVB(4) }
+  else if (nvec <= 8) { GS_NVB(8) }
+  else if (nvec <= 16) { GS_NVB(16) }
+  else if (nvec <= 32) { GS_NVB(32) }
+  else { GS_NVB(64) }
+#undef GS_NVB
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce(plan.blocks, (nvec + 1) * plan.nrhs, partials, out, skip, stream);
+}
+
+// ------------------------------------------------------------------ small streaming kernels
+
+__global__ void __launch_bounds__(256)
+sub_norm_kernel(int64_t n, int nrhs, const double2* __restrict__ b, const double2* __restrict__ t,
+                double2* __restrict__ r, double2* __restrict__ partials) {
+  double nn = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double2 bv = b[e], tv = t[e];
+    const double2 rv = make_double2(bv.x - tv.x, bv.y - tv.y);
+    r[e] = rv;
+    nn += rv.x * rv.x + rv.y * rv.y;
+  }
+  double vr[1] = {nn}, vi[1] = {0.0};
+  block_reduce_slots<1>(vr, vi, 1, nrhs, partials);
+}
+
+cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
+                            void* partials, void* out, cudaStream_t stream) {
+  sub_norm_kernel<<<plan.blocks, plan.threads, 0, stream>>>(
+      n, plan.nrhs, (const double2*)b, (const double2*)t, (double2*)r, (double2*)partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce(plan.blocks, plan.nrhs, partials, out, nullptr, stream);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256)
+norm2_kernel(int64_t n, int nrhs, const C* __restrict__ v, double2* __restrict__ partials) {
+  double nn = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const C x = v[e];
+    nn += (double)x.x * x.x + (double)x.y * x.y;
+  }
+  double vr[1] = {nn}, vi[1] = {0.0};
+  block_reduce_slots<1>(vr, vi, 1, nrhs, partials);
+}
+
+cudaError_t launch_norm2(bool f64, const BlasPlan& plan, int64_t n, const void* v, void* partials,
+                         void* out, cudaStream_t stream) {
+  if (f64)
+    norm2_kernel<double2><<<plan.blocks, plan.threads, 0, stream>>>(n, plan.nrhs, (const double2*)v,
+                                                                     (double2*)partials);
+  else
+    norm2_kernel<float2><<<plan.blocks, plan.threads, 0, stream>>>(n, plan.nrhs, (const float2*)v,
+                                                                    (double2*)partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce(plan.blocks, plan.nrhs, partials, out, nullptr, stream);
+}
+
+template <typename CD>
+__global__ void scale_convert_kernel(int64_t n, int nrhs, const double2* __restrict__ src,
+                                     const double* __restrict__ scale, CD* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double s = scale[e % nrhs];
+    const double2 v = src[e];
+    CD o;
+    o.x = v.x * s;
+    o.y = v.y * s;
+    dst[e] = o;
+  }
+}
+
+static int stream_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 152 * 16;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_scale_convert(bool dst_f64, int64_t n, int nrhs, const void* src,
+                                 const double* scale, void* dst, cudaStream_t stream) {
+  const int threads = 256;
+  const int blocks = stream_blocks(n, threads);
+  if (dst_f64)
+    scale_convert_kernel<double2><<<blocks, threads, 0, stream>>>(n, nrhs, (const double2*)src, scale,
+                                                                  (double2*)dst);
+  else
+    scale_convert_kernel<float2><<<blocks, threads, 0, stream>>>(n, nrhs, (const double2*)src, scale,
+                                                                 (float2*)dst);
+  return cudaGetLastError();
+}
+
+template <typename C>
+__global__ void scale_inplace_kernel(int64_t n, int nrhs, C* __restrict__ v,
+                                     const double* __restrict__ scale, const int* skip) {
+  if (skip != nullptr && *skip != 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double s = scale[e % nrhs];
+    C x = v[e];
+    x.x = x.x * s;
+    x.y = x.y * s;
+    v[e] = x;
+  }
+}
+
+cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const double* scale,
+                                 const int* skip, cudaStream_t stream) {
+  const int threads = 256;
+  const int blocks = stream_blocks(n, threads);
+  if (f64)
+    scale_inplace_kernel<double2><<<blocks, threads, 0, stream>>>(n, nrhs, (double2*)v, scale, skip);
+  else
+    scale_inplace_kernel<float2><<<blocks, threads, 0, stream>>>(n, nrhs, (float2*)v, scale, skip);
+  return cudaGetLastError();
+}
+
+// x += sum_i y[i][r] v_i with the sum formed in the basis precision (the
+// correction of one restart cycle; its rounding is removed by the next FP64
+// true residual) and added to x in FP64.
+template <typename C>
+__global__ void __launch_bounds__(256)
+update_x_kernel(int64_t n, int nrhs, const C* __restrict__ basis, int64_t vstride,
+                const double2* __restrict__ y, const int* __restrict__ kmax, double2* __restrict__ x) {
+  using Real = typename RealOf<C>::T;
+  extern __shared__ double2 ys[];
+  const int k = *kmax;
+  for (int q = threadIdx.x; q < k * nrhs; q += blockDim.x) ys[q] = y[q];
+  __syncthreads();
+  if (k == 0) return;
+  const int r = threadIdx.x % nrhs;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    Real sr = 0, si = 0;
+    for (int i = 0; i < k; ++i) {
+      const double2 c = ys[i * nrhs + r];
+      const C v = __ldg(basis + i * vstride + e);
+      const Real crr = (Real)c.x, cii = (Real)c.y;
+      sr += crr * v.x - cii * v.y;
+      si += crr * v.y + cii * v.x;
+    }
+    double2 xv = x[e];
+    xv.x += (double)sr;
+    xv.y += (double)si;
+    x[e] = xv;
+  }
+}
+
+cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
+                            int64_t vstride, const void* y, const int* kmax, void* x,
+                            cudaStream_t stream) {
+  const int threads = nrhs * (256 / nrhs);
+  const int blocks = stream_blocks(n, threads);
+  const size_t smem = sizeof(double2) * (size_t)nvec_max * nrhs;
+  if (basis_f64)
+    update_x_kernel<double2><<<blocks, threads, smem, stream>>>(n, nrhs, (const double2*)basis, vstride,
+                                                                (const double2*)y, kmax, (double2*)x);
+  else
+    update_x_kernel<float2><<<blocks, threads, smem, stream>>>(n, nrhs, (const float2*)basis, vstride,
+                                                               (const double2*)y, kmax, (double2*)x);
+  return cudaGetLastError();
+}
+
+template <typename CS, typename CD>
+__global__ void convert_kernel(int64_t n, const CS* __restrict__ src, CD* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const CS v = src[e];
+    CD o;
+    o.x = v.x;
+    o.y = v.y;
+    dst[e] = o;
+  }
+}
+
+cudaError_t launch_convert(bool to_f64, int64_t n, const void* src, void* dst, cudaStream_t stream) {
+  const int threads = 256;
+  const int blocks = stream_blocks(n, threads);
+  if (to_f64)
+    convert_kernel<float2, double2><<<blocks, threads, 0, stream>>>(n, (const float2*)src, (double2*)dst);
+  else
+    convert_kernel<double2, float2><<<blocks, threads, 0, stream>>>(n, (const double2*)src, (float2*)dst);
+  return cudaGetLastError();
+}
+
+}  // namespace lqcd

@@ -1,0 +1,85 @@
+// Library context and host-side helpers shared by the C ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/lqcd.h"
+#include "dslash.cuh"
+#include "kernels.h"
+
+namespace lqcd {
+
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::string key;
+};
+
+}  // namespace lqcd
+
+struct lqcd_ctx_s {
+  lqcd::Geom g;
+  int dims[4];
+  int time_bc = -1;
+  int num_sms = 152;
+  int device = 0;
+  bool have_gauge = false;
+  bool have_blocks = false;
+  double m0 = 0.0, c_sw = 0.0;
+  void* links64 = nullptr;  // [4][9][V] double2
+  void* links32 = nullptr;  // [4][9][V] float2
+  void* blk64 = nullptr;    // A, 72 doubles per site (SoA double2 chunks)
+  void* inv64 = nullptr;    // A^{-1}
+  void* blk32 = nullptr;    // A, 72 floats per site (SoA float4 chunks)
+  void* inv32 = nullptr;
+  int* d_err = nullptr;     // device status bitmask
+  std::map<std::string, lqcd::Buffer> ws;
+  cudaStream_t capture_stream = nullptr;
+  lqcd::CycleGraph cycle;
+  std::vector<cudaEvent_t> prof_events;  // solver profiling events (4 per Arnoldi step)
+  void* pinned = nullptr;   // small pinned host staging area
+  size_t pinned_bytes = 0;
+};
+
+namespace lqcd {
+
+// Error reporting (thread-local message for lqcd_last_error).
+lqcd_status set_error(lqcd_status s, const char* fmt, ...);
+lqcd_status cuda_error(cudaError_t e, const char* what);
+#define LQCD_CUDA(call, what)                              \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return lqcd::cuda_error(_e, what); \
+  } while (0)
+
+// Grow-only named device workspace.
+lqcd_status workspace(lqcd_ctx ctx, const char* name, size_t bytes, void** out);
+lqcd_status pinned_staging(lqcd_ctx ctx, size_t bytes, void** out);
+
+int site_tile_log2(const lqcd_ctx_s* ctx, int nrhs);
+PackedLayout layout_for(const lqcd_ctx_s* ctx, int nrhs);
+bool is_device_pointer(const void* p);
+
+// Operator application on packed blocks (used by the apply entry points and the solver).
+//   op FULL: in/out full blocks. op SCHUR: in/out odd blocks, tmp = even-half scratch.
+lqcd_status apply_operator(lqcd_ctx ctx, int op, bool f64, int nrhs, const void* in, void* out,
+                           void* tmp, const int* skip, cudaStream_t stream);
+lqcd_status schur_prepare(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, void* bhat_o,
+                          void* tmp_even, cudaStream_t stream);
+lqcd_status schur_reconstruct(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, const void* x_o,
+                              void* x_full, cudaStream_t stream);
+
+inline size_t packed_elems(const lqcd_ctx_s* ctx, int sites, int nrhs) {
+  const size_t ns = sites == LQCD_SITES_FULL ? (size_t)ctx->g.V : (size_t)ctx->g.Vh;
+  return ns * 12 * (size_t)nrhs;
+}
+
+}  // namespace lqcd

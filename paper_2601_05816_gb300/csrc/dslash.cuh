@@ -1,0 +1,336 @@
+// Multi-rhs Wilson(-clover) hopping kernel (Sec. III-A-1, Algorithm 1, Eq. (1)-(2)).
+//
+// One kernel computes, for every target site x and every rhs,
+//   out(x) = POST( SELF(self_in)(x) + c_hop * H(hop_in)(x) ),
+//   H(psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+// SELF in {none, sigma * 1, A(x)}, POST in {none, tau * 1, A(x)^{-1}}. With
+// c_hop = -1/2 this is the paper's D = (4 + m0) - C - sum_mu [pi^- U + pi^+ U^dag]
+// (pi^+- = (1 +- gamma)/2). The odd-even passes of Sec. III-A-2 are the same
+// kernel restricted to one parity:
+//   pass A  t_e = A_ee^{-1} D_eo psi_o:  SELF none,  c_hop = -1/2, POST A^{-1}
+//   pass B  out = A_oo psi_o - D_oe t_e: SELF A,     c_hop = +1/2, POST none
+//   prepare hat b_o = b_o - D_oe u_e:    SELF 1,     c_hop = +1/2
+//   reconstruct x_e = A^{-1}(b_e - D_eo x_o): SELF 1, c_hop = +1/2, POST A^{-1}
+//
+// GPU mapping. Thread (site, rhs group): threadIdx.x picks NR consecutive rhs,
+// threadIdx.y the site. The packed spinor layout stores the rhs innermost, so
+// the threads of one site read one contiguous run per spin-colour component
+// (16-byte vector loads for NR = 2 in FP32 and for FP64), and every lane of a
+// site loads the same link and clover entries: the warp broadcasts them, which
+// is the paper's "link read once per b rhs". Spin projection (Algorithm 1's
+// lambda/chi with 6 of 12 components), the SU(3) multiply on the two projected
+// spin components and the reconstruction to 12 components all stay in
+// registers; the half spinors are never written to memory. Neighbour halos come
+// from L1/L2: each spinor is used by its eight neighbours, which the lexicographic
+// thread order keeps within a few time slices, well inside the 129 MB L2.
+#pragma once
+#include "common.cuh"
+
+namespace lqcd {
+
+enum { SELF_NONE = 0, SELF_SCALAR = 1, SELF_BLOCK = 2 };
+enum { POST_NONE = 0, POST_SCALAR = 1, POST_BLOCKINV = 2 };
+
+template <typename Real>
+struct DslashArgs {
+  using C = typename Cplx<Real>::T;
+  Geom g;
+  PackedLayout lay;
+  int n_target;        // V (full) or V/2 (one parity)
+  int full;            // 1: targets are all sites, blocks hold even then odd half
+  int target_parity;   // parity of the targets when full == 0
+  int hop;             // 0: skip the hopping term (site-local operator only)
+  int64_t half_elems;  // complex elements in one parity's half of a packed block
+  C* out;
+  const C* self_in;    // indexed like out
+  const C* hop_in;     // full: full block; else the block of the opposite parity
+  const C* links;      // [4][9][V] complex, eo site order, time boundary factor folded in
+  const Real* blocks;      // A(x): 72 reals per site, SoA in 16-byte chunks [72*sizeof/16][V]
+  const Real* blocks_inv;  // A(x)^{-1}, same layout
+  Real self_scalar, post_scalar, c_hop;
+  const int* skip;     // optional: return at once when *skip != 0
+};
+
+// NR complex numbers (NR consecutive rhs of one component).
+template <typename Real, int NR>
+struct MC {
+  Real re[NR], im[NR];
+};
+
+template <typename Real, int NR>
+__device__ __forceinline__ void mc_zero(MC<Real, NR>& a) {
+#pragma unroll
+  for (int k = 0; k < NR; ++k) { a.re[k] = 0; a.im[k] = 0; }
+}
+
+// a += coef * b, coef code: 0 -> +1, 1 -> -1, 2 -> +i, 3 -> -i
+template <int CODE, typename Real, int NR>
+__device__ __forceinline__ void mc_acc(MC<Real, NR>& a, const MC<Real, NR>& b) {
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    if (CODE == 0) { a.re[k] += b.re[k]; a.im[k] += b.im[k]; }
+    if (CODE == 1) { a.re[k] -= b.re[k]; a.im[k] -= b.im[k]; }
+    if (CODE == 2) { a.re[k] -= b.im[k]; a.im[k] += b.re[k]; }
+    if (CODE == 3) { a.re[k] += b.im[k]; a.im[k] -= b.re[k]; }
+  }
+}
+
+template <int CODE, typename Real, int NR>
+__device__ __forceinline__ MC<Real, NR> mc_comb(const MC<Real, NR>& a, const MC<Real, NR>& b) {
+  MC<Real, NR> r = a;
+  mc_acc<CODE>(r, b);
+  return r;
+}
+
+// Vector loads / stores of NR consecutive complex numbers.
+__device__ __forceinline__ void mc_load(MC<float, 2>& a, const float2* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a.re[0] = v.x; a.im[0] = v.y; a.re[1] = v.z; a.im[1] = v.w;
+}
+__device__ __forceinline__ void mc_load(MC<float, 1>& a, const float2* p) {
+  float2 v = __ldg(p);
+  a.re[0] = v.x; a.im[0] = v.y;
+}
+__device__ __forceinline__ void mc_load(MC<double, 1>& a, const double2* p) {
+  double2 v = __ldg(p);
+  a.re[0] = v.x; a.im[0] = v.y;
+}
+__device__ __forceinline__ void mc_store(float2* p, const MC<float, 2>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.re[0], a.im[0], a.re[1], a.im[1]);
+}
+__device__ __forceinline__ void mc_store(float2* p, const MC<float, 1>& a) {
+  *p = make_float2(a.re[0], a.im[0]);
+}
+__device__ __forceinline__ void mc_store(double2* p, const MC<double, 1>& a) {
+  *p = make_double2(a.re[0], a.im[0]);
+}
+
+// Spin structure of 1 -+ gamma_mu in the chiral basis gamma = [[0, P], [P^dag, 0]]
+// (P_t = 1, P_z = i sigma_z, P_y = i sigma_y, P_x = i sigma_x), with spins
+// u0, u1 (upper) and d0, d1 (lower):
+//   forward (1 - gamma):  h = u - P d;       lower part of the result = -P^dag (U h)
+//   backward (1 + gamma): k = u + P d;       lower part of the result = +P^dag (U^dag k)
+// Projection h_s = u_s + coef * d_src, reconstruction low_s += coef * (Uh)_src;
+// the backward coefficients are the negatives of the forward ones.
+template <int MU> struct SpinTab;
+//                       proj: src0 coef0 src1 coef1   recon: src0 coef0 src1 coef1
+template <> struct SpinTab<0> { enum { ps0 = 0, pc0 = 1, ps1 = 1, pc1 = 1, rs0 = 0, rc0 = 1, rs1 = 1, rc1 = 1 }; };
+template <> struct SpinTab<1> { enum { ps0 = 0, pc0 = 3, ps1 = 1, pc1 = 2, rs0 = 0, rc0 = 2, rs1 = 1, rc1 = 3 }; };
+template <> struct SpinTab<2> { enum { ps0 = 1, pc0 = 1, ps1 = 0, pc1 = 0, rs0 = 1, rc0 = 0, rs1 = 0, rc1 = 1 }; };
+template <> struct SpinTab<3> { enum { ps0 = 1, pc0 = 3, ps1 = 0, pc1 = 3, rs0 = 1, rc0 = 2, rs1 = 0, rc1 = 2 }; };
+
+__host__ __device__ constexpr int neg_code(int c) { return c == 0 ? 1 : c == 1 ? 0 : c == 2 ? 3 : 2; }
+
+// One hopping direction (forward for DIR = +1, backward for DIR = -1).
+template <typename Real, int NR, int MU, int DIR>
+__device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
+                                        const typename Cplx<Real>::T* hin, MC<Real, NR> acc[12]) {
+  using C = typename Cplx<Real>::T;
+  using Tab = SpinTab<MU>;
+  const int nlex = neighbour_lex<MU, DIR>(a.g, c);
+  const int ncb = nlex >> 1;
+  // link: U_mu(x) forward, U_mu(x - mu) backward (eo index of its base site)
+  const int link_site = (DIR > 0) ? (p * a.g.Vh + (c.lex >> 1)) : ((1 - p) * a.g.Vh + ncb);
+  const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
+  C u[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
+
+  // neighbour spinor: upper spins (comps 0..5), lower spins (comps 6..11)
+  MC<Real, NR> up[6], dn[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    mc_load(up[k], hin + a.lay.index(ncb, k, r0));
+    mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+  }
+  constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);
+  constexpr int pc1 = DIR > 0 ? Tab::pc1 : neg_code(Tab::pc1);
+  constexpr int rc0 = DIR > 0 ? Tab::rc0 : neg_code(Tab::rc0);
+  constexpr int rc1 = DIR > 0 ? Tab::rc1 : neg_code(Tab::rc1);
+  MC<Real, NR> h[6];  // [spin s in 0,1][colour]
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    h[col] = mc_comb<pc0>(up[col], dn[3 * Tab::ps0 + col]);
+    h[3 + col] = mc_comb<pc1>(up[3 + col], dn[3 * Tab::ps1 + col]);
+  }
+  MC<Real, NR> w[6];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int ar = 0; ar < 3; ++ar) {
+      MC<Real, NR>& o = w[3 * s + ar];
+      mc_zero(o);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // forward: U[ar][b] * h_b ; backward: conj(U[b][ar]) * h_b
+        const C m = (DIR > 0) ? u[3 * ar + b] : u[3 * b + ar];
+        const Real mr = m.x;
+        const Real mi = (DIR > 0) ? m.y : -m.y;
+        const MC<Real, NR>& v = h[3 * s + b];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+          o.re[k] = fma(mr, v.re[k], o.re[k]);
+          o.re[k] = fma(-mi, v.im[k], o.re[k]);
+          o.im[k] = fma(mr, v.im[k], o.im[k]);
+          o.im[k] = fma(mi, v.re[k], o.im[k]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    mc_acc<0>(acc[col], w[col]);
+    mc_acc<0>(acc[3 + col], w[3 + col]);
+    mc_acc<rc0>(acc[6 + col], w[3 * Tab::rs0 + col]);
+    mc_acc<rc1>(acc[9 + col], w[3 * Tab::rs1 + col]);
+  }
+}
+
+// Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 strictly
+// lower entries L(l, j), l > j, in the order (1,0), (2,0), (2,1), (3,0), ...
+// (index l(l-1)/2 + j) as (re, im) pairs: 36 reals. Site blocks hold the upper
+// chiral block (spins 0, 1) then the lower one (spins 2, 3): 72 reals.
+template <typename Real, int NR>
+__device__ __forceinline__ void block_matvec(const Real* m, const MC<Real, NR>* x, MC<Real, NR>* y) {
+#pragma unroll
+  for (int l = 0; l < 6; ++l) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) { y[l].re[k] = m[l] * x[l].re[k]; y[l].im[k] = m[l] * x[l].im[k]; }
+  }
+#pragma unroll
+  for (int l = 1; l < 6; ++l) {
+#pragma unroll
+    for (int j = 0; j < l; ++j) {
+      const Real lr = m[6 + 2 * (l * (l - 1) / 2 + j)];
+      const Real li = m[6 + 2 * (l * (l - 1) / 2 + j) + 1];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        // y_l += L_lj x_j
+        y[l].re[k] = fma(lr, x[j].re[k], y[l].re[k]);
+        y[l].re[k] = fma(-li, x[j].im[k], y[l].re[k]);
+        y[l].im[k] = fma(lr, x[j].im[k], y[l].im[k]);
+        y[l].im[k] = fma(li, x[j].re[k], y[l].im[k]);
+        // y_j += conj(L_lj) x_l
+        y[j].re[k] = fma(lr, x[l].re[k], y[j].re[k]);
+        y[j].re[k] = fma(li, x[l].im[k], y[j].re[k]);
+        y[j].im[k] = fma(lr, x[l].im[k], y[j].im[k]);
+        y[j].im[k] = fma(-li, x[l].re[k], y[j].im[k]);
+      }
+    }
+  }
+}
+
+// Load one chiral half (36 reals) of a site's packed block.
+__device__ __forceinline__ void load_half_block(float* dst, const float* blocks, int V, int site, int half) {
+  const float4* b4 = reinterpret_cast<const float4*>(blocks);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    float4 v = __ldg(b4 + (int64_t)(9 * half + k) * V + site);
+    dst[4 * k] = v.x; dst[4 * k + 1] = v.y; dst[4 * k + 2] = v.z; dst[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_half_block(double* dst, const double* blocks, int V, int site, int half) {
+  const double2* b2 = reinterpret_cast<const double2*>(blocks);
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    double2 v = __ldg(b2 + (int64_t)(18 * half + k) * V + site);
+    dst[2 * k] = v.x; dst[2 * k + 1] = v.y;
+  }
+}
+
+template <typename Real, int NR>
+__device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int site,
+                                                 const MC<Real, NR> x[12], MC<Real, NR> y[12]) {
+  Real m[36];
+  load_half_block(m, blocks, V, site, 0);
+  block_matvec<Real, NR>(m, x, y);
+  load_half_block(m, blocks, V, site, 1);
+  block_matvec<Real, NR>(m, x + 6, y + 6);
+}
+
+template <typename Real, int NR, int SELF, int POST>
+__global__ void __launch_bounds__(256) dslash_kernel(DslashArgs<Real> a) {
+  using C = typename Cplx<Real>::T;
+  if (a.skip != nullptr && *a.skip != 0) return;
+  const int site = blockIdx.x * blockDim.y + threadIdx.y;
+  if (site >= a.n_target) return;
+  const int r0 = threadIdx.x * NR;
+  int p, cb;
+  if (a.full) {
+    p = site >= a.g.Vh ? 1 : 0;
+    cb = site - p * a.g.Vh;
+  } else {
+    p = a.target_parity;
+    cb = site;
+  }
+  const int eo_site = p * a.g.Vh + cb;
+
+  MC<Real, NR> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) mc_zero(acc[k]);
+
+  if (a.hop) {
+    const Coord c = site_coords(a.g, p, cb);
+    const C* hin = a.full ? a.hop_in + (1 - p) * a.half_elems : a.hop_in;
+    hop_dir<Real, NR, 0, +1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, -1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, +1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, -1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, +1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, -1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, +1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, -1>(a, c, p, r0, hin, acc);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) { acc[k].re[q] *= a.c_hop; acc[k].im[q] *= a.c_hop; }
+  }
+
+  const int64_t base = a.full ? p * a.half_elems : 0;
+  if (SELF != SELF_NONE) {
+    const C* sp = a.self_in + base;
+    MC<Real, NR> s[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mc_load(s[k], sp + a.lay.index(cb, k, r0));
+    if (SELF == SELF_SCALAR) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          acc[k].re[q] = fma(a.self_scalar, s[k].re[q], acc[k].re[q]);
+          acc[k].im[q] = fma(a.self_scalar, s[k].im[q], acc[k].im[q]);
+        }
+    } else {
+      MC<Real, NR> t[12];
+      site_block_apply<Real, NR>(a.blocks, a.g.V, eo_site, s, t);
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) { acc[k].re[q] += t[k].re[q]; acc[k].im[q] += t[k].im[q]; }
+    }
+  }
+
+  C* op = a.out + base;
+  if (POST == POST_BLOCKINV) {
+    MC<Real, NR> t[12];
+    site_block_apply<Real, NR>(a.blocks_inv, a.g.V, eo_site, acc, t);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) mc_store(op + a.lay.index(cb, k, r0), t[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if (POST == POST_SCALAR) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) { acc[k].re[q] *= a.post_scalar; acc[k].im[q] *= a.post_scalar; }
+      }
+      mc_store(op + a.lay.index(cb, k, r0), acc[k]);
+    }
+  }
+}
+
+// Host-side launcher, instantiated in dslash_f32.cu / dslash_f64.cu.
+template <typename Real>
+cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mode, int nr,
+                          cudaStream_t stream);
+
+}  // namespace lqcd

@@ -1,0 +1,26 @@
+// FP64 (complex128) instantiations of the multi-rhs hopping kernel.
+#include "dslash.cuh"
+#include "kernels.h"
+
+namespace lqcd {
+
+template <>
+cudaError_t launch_dslash<double>(const DslashArgs<double>& a, int self_mode, int post_mode, int nr,
+                                  cudaStream_t s) {
+  (void)nr;
+  const int G = a.lay.nrhs;
+  dim3 block(G, G >= 128 ? 1 : 128 / G);
+  dim3 grid((a.n_target + block.y - 1) / block.y);
+#define DS(SM, PM) dslash_kernel<double, 1, SM, PM><<<grid, block, 0, s>>>(a)
+  if (self_mode == SELF_SCALAR && post_mode == POST_NONE) DS(SELF_SCALAR, POST_NONE);
+  else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) DS(SELF_BLOCK, POST_NONE);
+  else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) DS(SELF_NONE, POST_SCALAR);
+  else if (self_mode == SELF_NONE && post_mode == POST_BLOCKINV) DS(SELF_NONE, POST_BLOCKINV);
+  else if (self_mode == SELF_SCALAR && post_mode == POST_SCALAR) DS(SELF_SCALAR, POST_SCALAR);
+  else if (self_mode == SELF_SCALAR && post_mode == POST_BLOCKINV) DS(SELF_SCALAR, POST_BLOCKINV);
+  else return cudaErrorInvalidValue;
+#undef DS
+  return cudaGetLastError();
+}
+
+}  // namespace lqcd

@@ -1,0 +1,88 @@
+// Internal launcher declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lqcd {
+
+// pack.cu
+cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, bool to_packed,
+                                 bool f64, const void* in, void* out, cudaStream_t stream);
+cudaError_t launch_gauge_pack(const Geom& g, int time_bc, const void* U, void* l64, void* l32,
+                              cudaStream_t stream);
+
+// clover.cu: site blocks A = (4 + m0) - C and A^{-1}, FP64 then FP32 copies.
+// leaf_tmp: device scratch of 6 * 9 * V complex128. err_flag: device int (bitmask).
+cudaError_t launch_clover_build(const Geom& g, const void* links64, double m0, double c_sw,
+                                void* leaf_tmp, void* blk64, void* inv64, void* blk32, void* inv32,
+                                int* err_flag, cudaStream_t stream);
+cudaError_t launch_blocks_export(const Geom& g, const void* blk64, void* out, cudaStream_t stream);
+
+// blas.cu: multi-rhs vector kernels on packed blocks of n complex elements
+// (rhs of element e is e % nrhs). Reductions go to per-CTA partials, then
+// reduce_partials sums them in a fixed order (deterministic).
+struct BlasPlan {
+  int nrhs;
+  int threads;   // multiple of nrhs, <= 256
+  int blocks;    // CTAs of the streaming kernels
+};
+BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
+
+// Fused block Gram-Schmidt pass over nvec basis vectors v_i = basis + i * vstride:
+//   if update: w <- w - sum_i coef[i][r] v_i   (coef: device double2 [nvec][nrhs])
+//   if dots:   out[i][r] = <v_i, w>  (after the update)
+//   if norm:   out[nvec][r] = ||w||^2 (real part)
+// out: device double2 [nvec + 1][nrhs]; partials: device scratch double2
+// [plan.blocks][nvec + 1][nrhs]. skip: optional device flag (return when set).
+cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
+                           int64_t vstride, void* w, const void* coef, bool update, bool dots,
+                           bool norm, void* partials, void* out, const int* skip,
+                           cudaStream_t stream);
+
+// r = b - t (all FP64) with out[0][r] = ||r||^2.
+cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
+                            void* partials, void* out, cudaStream_t stream);
+// ||v||^2 per rhs, out[0][r]; v in FP64 or FP32.
+cudaError_t launch_norm2(bool f64, const BlasPlan& plan, int64_t n, const void* v, void* partials,
+                         void* out, cudaStream_t stream);
+// dst[e] = (dst precision) (src[e] * scale[r]); src FP64, dst FP64 or FP32.
+cudaError_t launch_scale_convert(bool dst_f64, int64_t n, int nrhs, const void* src,
+                                 const double* scale, void* dst, cudaStream_t stream);
+// v[e] *= scale[r] in place (v FP64 or FP32).
+cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const double* scale,
+                                 const int* skip, cudaStream_t stream);
+// x[e] += sum_{i < *kmax} y[i][r] v_i[e]; x FP64, basis FP64 or FP32 (sum in basis precision).
+cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
+                            int64_t vstride, const void* y, const int* kmax, void* x,
+                            cudaStream_t stream);
+// Widen / narrow copies between FP64 and FP32 packed blocks.
+cudaError_t launch_convert(bool to_f64, int64_t n, const void* src, void* dst, cudaStream_t stream);
+
+// gmres.cu: per-rhs small dense work of Algorithm 2 in FP64 on the device.
+struct GmresState {
+  int m, nrhs;
+  double2* H;        // [nrhs][m][m + 1]: column j of the rotated Hessenberg matrix
+  double* cs;        // [nrhs][m]
+  double2* sn;       // [nrhs][m]
+  double2* gamma;    // [nrhs][m + 1]
+  double2* y;        // [m][nrhs]
+  double* thr;       // [nrhs] absolute stop threshold of the cycle
+  double* scale;     // [nrhs] 1 / beta for the next basis vector (0 = inactive)
+  int* active;       // [nrhs]
+  int* done;         // [nrhs] cycle finished for this rhs
+  int* k;            // [nrhs] Arnoldi steps taken in this cycle
+  int* all_done;     // [1]
+  int* kmax;         // [1]
+};
+// init: gamma = (beta0, 0, ...), done = !active, scale = active / beta0.
+cudaError_t launch_cycle_init(const GmresState& s, const double* beta0, cudaStream_t stream);
+// step j: column from h1 (+ h2 when h2 != null) and ||w||^2 = hn[j + 1][r], rotations, gamma, stop test.
+cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void* h2, const void* hn,
+                          cudaStream_t stream);
+cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream);
+
+// dslash_f32.cu / dslash_f64.cu: see dslash.cuh.
+
+}  // namespace lqcd

@@ -1,0 +1,622 @@
+// Batched restarted GMRES (Algorithm 2) on the GPU, with optional odd-even
+// preconditioning (Sec. III-A-2) and FP32-inside-FP64 iterative refinement.
+//
+// Structure of one solve (every rhs independent, as in the paper's batched solver):
+//   restart: r = b - D x in FP64 (FP64 operator), ||r|| per rhs; the host reads
+//            the norms (one stream synchronisation per restart), retires the rhs
+//            whose true residual meets tol, and starts a cycle for the others
+//            with v_0 = r / ||r|| stored in the inner precision;
+//   cycle:   m Arnoldi steps, each = operator apply (inner precision) + block
+//            classical Gram-Schmidt with one re-orthogonalisation (CGS2, fused
+//            dot/update passes) + a device kernel that updates the Hessenberg
+//            column with the stored Givens rotations, forms the new rotation and
+//            gamma, and tests |gamma_{j+1}| against the cycle threshold per rhs
+//            (rhs that met it stop contributing: their next basis vector is 0);
+//            the whole cycle can be replayed as one captured CUDA graph;
+//   update:  back substitution (FP64, device) and x += V y with x in FP64.
+// In FP64 mode the inner precision is FP64 and this is plain restarted GMRES;
+// in FP32 mode it is GMRES-based iterative refinement: FP64 stays on the true
+// residual, the solution update and the small Givens / least-squares step.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ small dense kernels
+
+__global__ void cycle_init_kernel(GmresState s, const double* __restrict__ beta0) {
+  const int r = threadIdx.x;
+  bool live = false;
+  if (r < s.nrhs) {
+    const int act = s.active[r];
+    for (int i = 0; i <= s.m; ++i) s.gamma[(int64_t)r * (s.m + 1) + i] = make_double2(0, 0);
+    s.gamma[(int64_t)r * (s.m + 1)] = make_double2(act ? beta0[r] : 0.0, 0.0);
+    s.done[r] = act ? 0 : 1;
+    s.k[r] = 0;
+    s.scale[r] = act ? 1.0 / beta0[r] : 0.0;
+    live = act != 0;
+  }
+  const int any = __syncthreads_or(live);
+  if (threadIdx.x == 0) {
+    *s.all_done = any ? 0 : 1;
+    *s.kmax = 0;
+  }
+}
+
+// Column j of the Hessenberg matrix from the Gram-Schmidt coefficients, the
+// stored rotations applied to it, a new rotation (c = |a|/rho, s = (a/|a|) h/rho),
+// gamma_{j+1} = -conj(s) gamma_j, gamma_j = c gamma_j, and the stop test.
+__global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h1,
+                              const double2* __restrict__ h2, const double2* __restrict__ hn) {
+  const int r = threadIdx.x;
+  const int nrhs = s.nrhs;
+  bool live = false;
+  if (r < nrhs) {
+    if (!s.done[r]) {
+      double2* col = s.H + ((int64_t)r * s.m + j) * (s.m + 1);
+      double w2 = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        double2 v = h1[(int64_t)i * nrhs + r];
+        if (h2 != nullptr) {
+          const double2 u = h2[(int64_t)i * nrhs + r];
+          v.x += u.x;
+          v.y += u.y;
+        }
+        col[i] = v;
+        w2 += v.x * v.x + v.y * v.y;
+      }
+      const double beta2 = fmax(hn[(int64_t)(j + 1) * nrhs + r].x, 0.0);
+      const double beta = sqrt(beta2);
+      w2 += beta2;
+      double* cs = s.cs + (int64_t)r * s.m;
+      double2* sn = s.sn + (int64_t)r * s.m;
+      for (int i = 0; i < j; ++i) {
+        const double2 top = col[i], bot = col[i + 1];
+        const double c = cs[i];
+        const double2 sv = sn[i];
+        // top' = c top + s bot ; bot' = -conj(s) top + c bot
+        col[i] = make_double2(c * top.x + sv.x * bot.x - sv.y * bot.y, c * top.y + sv.x * bot.y + sv.y * bot.x);
+        col[i + 1] = make_double2(-(sv.x * top.x + sv.y * top.y) + c * bot.x,
+                                  -(sv.x * top.y - sv.y * top.x) + c * bot.y);
+      }
+      const double2 a = col[j];
+      const double aa = hypot(a.x, a.y);
+      const double rho = hypot(aa, beta);
+      double c;
+      double2 sv, rjj;
+      if (rho == 0.0) {
+        c = 1.0; sv = make_double2(0, 0); rjj = make_double2(0, 0);
+      } else if (aa == 0.0) {
+        c = 0.0; sv = make_double2(1, 0); rjj = make_double2(rho, 0);
+      } else {
+        const double2 ph = make_double2(a.x / aa, a.y / aa);
+        c = aa / rho;
+        sv = make_double2(ph.x * beta / rho, ph.y * beta / rho);
+        rjj = make_double2(ph.x * rho, ph.y * rho);
+      }
+      cs[j] = c;
+      sn[j] = sv;
+      col[j] = rjj;
+      double2* gm = s.gamma + (int64_t)r * (s.m + 1);
+      const double2 gj = gm[j];
+      gm[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+      gm[j] = make_double2(c * gj.x, c * gj.y);
+      s.k[r] = j + 1;
+      const double res = hypot(gm[j + 1].x, gm[j + 1].y);
+      const bool bad = !(isfinite(res) && isfinite(beta));
+      const bool stop = bad || res <= s.thr[r] || beta <= 1e-14 * sqrt(w2) || j == s.m - 1;
+      if (stop) {
+        s.done[r] = 1;
+        s.scale[r] = 0.0;
+        if (bad) s.k[r] = j;  // discard the step that produced a non-finite value
+      } else {
+        s.scale[r] = 1.0 / beta;
+        live = true;
+      }
+    } else {
+      s.scale[r] = 0.0;
+    }
+  }
+  const int any = __syncthreads_or(live);
+  if (threadIdx.x == 0) *s.all_done = any ? 0 : 1;
+}
+
+// Back substitution R y = gamma per rhs; y stored [m][nrhs]; kmax = max_r k_r.
+__global__ void backsub_kernel(GmresState s) {
+  const int r = threadIdx.x;
+  int kr = 0;
+  if (r < s.nrhs) {
+    kr = s.k[r];
+    double2 yv[64];
+    for (int i = kr - 1; i >= 0; --i) {
+      double2 acc = s.gamma[(int64_t)r * (s.m + 1) + i];
+      for (int l = i + 1; l < kr; ++l) {
+        const double2 h = s.H[((int64_t)r * s.m + l) * (s.m + 1) + i];
+        acc.x -= h.x * yv[l].x - h.y * yv[l].y;
+        acc.y -= h.x * yv[l].y + h.y * yv[l].x;
+      }
+      const double2 d = s.H[((int64_t)r * s.m + i) * (s.m + 1) + i];
+      const double den = d.x * d.x + d.y * d.y;
+      yv[i] = den > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                        : make_double2(0.0, 0.0);
+    }
+    for (int i = 0; i < s.m; ++i) s.y[(int64_t)i * s.nrhs + r] = i < kr ? yv[i] : make_double2(0, 0);
+  }
+  __shared__ int kmax_s;
+  if (threadIdx.x == 0) kmax_s = 0;
+  __syncthreads();
+  if (r < s.nrhs) atomicMax(&kmax_s, kr);
+  __syncthreads();
+  if (threadIdx.x == 0) *s.kmax = kmax_s;
+}
+
+__global__ void combine_h_kernel(int nvec, int nrhs, const double2* h1, const double2* h2,
+                                 const double2* hn, double2* h, double* hnorm) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nvec * nrhs) {
+    double2 v = h1[q];
+    if (h2) { v.x += h2[q].x; v.y += h2[q].y; }
+    h[q] = v;
+  }
+  if (q < nrhs) hnorm[q] = sqrt(fmax(hn[(int64_t)nvec * nrhs + q].x, 0.0));
+}
+
+static int round_threads(int n) { return ((n + 31) / 32) * 32; }
+
+cudaError_t launch_cycle_init(const GmresState& s, const double* beta0, cudaStream_t stream) {
+  cycle_init_kernel<<<1, round_threads(s.nrhs), 0, stream>>>(s, beta0);
+  return cudaGetLastError();
+}
+cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void* h2, const void* hn,
+                          cudaStream_t stream) {
+  givens_kernel<<<1, round_threads(s.nrhs), 0, stream>>>(s, j, (const double2*)h1, (const double2*)h2,
+                                                         (const double2*)hn);
+  return cudaGetLastError();
+}
+cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream) {
+  backsub_kernel<<<1, round_threads(s.nrhs), 0, stream>>>(s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ solver pieces
+
+struct SolveBufs {
+  bool f64_inner;
+  int nrhs, m;
+  int64_t n_sys;        // complex elements of the system vector
+  size_t inner_bytes;   // bytes per inner basis vector
+  void* basis;          // (m + 1) inner vectors
+  void* tmp_even_in;    // Schur scratch, inner precision
+  void* tmp_even_64;    // Schur scratch, FP64
+  void* partials;
+  void* h1;             // [m + 1][nrhs] double2 each
+  void* h2;
+  void* hn;
+  GmresState st;
+  BlasPlan plan;
+};
+
+// Gram-Schmidt of basis[j+1] against basis[0..j] (CGS2 or CGS1), then the Givens step.
+static lqcd_status arnoldi_ortho(lqcd_ctx ctx, const SolveBufs& b, int j, bool reorth, cudaStream_t s) {
+  const int nvec = j + 1;
+  char* base = (char*)b.basis;
+  void* w = base + (size_t)(j + 1) * b.inner_bytes;
+  const int64_t vstride = b.n_sys;
+  const int* skip = b.st.all_done;
+  LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, nullptr, false, true,
+                           false, b.partials, b.h1, skip, s),
+            "gs dots");
+  if (reorth) {
+    LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, true,
+                             false, b.partials, b.h2, skip, s),
+              "gs update+dots");
+    LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h2, true, false,
+                             true, b.partials, b.hn, skip, s),
+              "gs update+norm");
+  } else {
+    LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, false,
+                             true, b.partials, b.hn, skip, s),
+              "gs update+norm");
+  }
+  (void)ctx;
+  return LQCD_OK;
+}
+
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // 4 per step: op start/end, gs start/end
+  double op_ms = 0, gs_ms = 0;
+  double op_bytes = 0, gs_bytes = 0;
+  int op_n = 0, gs_n = 0;
+  int used = 0;
+};
+
+// Algorithmic bytes (each operand moved once) of one operator apply on a packed block:
+// full: (48 b + 144) s per site with clover, (48 b + 72) s without;
+// Schur: (120 b + 432) s per odd site with clover, (120 b + 288) s without
+// (s = bytes per real; spinors read/written once per pass, 18 reals per link,
+// 72 reals per site block).
+static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int nrhs) {
+  const double s = f64 ? 8.0 : 4.0;
+  const bool clover = ctx->c_sw != 0.0;
+  if (op == LQCD_OP_FULL) return (double)ctx->g.V * (48.0 * nrhs + (clover ? 144.0 : 72.0)) * s;
+  return (double)ctx->g.Vh * (120.0 * nrhs + (clover ? 432.0 : 288.0)) * s;
+}
+
+// Algorithmic bytes of the Gram-Schmidt step with nvec basis vectors on n complex
+// elements: dots read nvec + 1 vectors; each update pass reads nvec + 1 and writes 1.
+static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, bool reorth) {
+  const double v = (double)n * (f64 ? 16.0 : 8.0);
+  const double dots = (nvec + 1) * v, upd = (nvec + 2) * v;
+  return reorth ? dots + 2 * upd : dots + upd;
+}
+
+static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bool reorth, Profile* prof,
+                                    cudaStream_t s) {
+  char* base = (char*)b.basis;
+  for (int j = 0; j < b.m; ++j) {
+    void* vj = base + (size_t)j * b.inner_bytes;
+    void* w = base + (size_t)(j + 1) * b.inner_bytes;
+    if (prof->on) LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 0], s), "event");
+    lqcd_status st = apply_operator(ctx, op, b.f64_inner, b.nrhs, vj, w, b.tmp_even_in, b.st.all_done, s);
+    if (st != LQCD_OK) return st;
+    if (prof->on) {
+      LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 1], s), "event");
+      LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 2], s), "event");
+    }
+    st = arnoldi_ortho(ctx, b, j, reorth, s);
+    if (st != LQCD_OK) return st;
+    if (prof->on) LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 3], s), "event");
+    LQCD_CUDA(launch_givens(b.st, j, b.h1, reorth ? b.h2 : nullptr, b.hn, s), "givens");
+    LQCD_CUDA(launch_scale_inplace(b.f64_inner, b.n_sys, b.nrhs, w, b.st.scale, b.st.all_done, s), "scale");
+  }
+  if (prof->on) prof->used = b.m;
+  return LQCD_OK;
+}
+
+static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reorth, bool use_graph,
+                             Profile* prof, cudaStream_t s) {
+  if (!use_graph) return run_cycle_direct(ctx, b, op, reorth, prof, s);
+  char key[256];
+  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%d/%p/%p/%p/%lld", op, (int)b.f64_inner, b.nrhs, b.m, (int)reorth,
+           (int)prof->on, b.basis, b.partials, (void*)b.st.H, (long long)b.n_sys);
+  if (ctx->cycle.exec == nullptr || ctx->cycle.key != key) {
+    if (ctx->cycle.exec) {
+      cudaGraphExecDestroy(ctx->cycle.exec);
+      cudaGraphDestroy(ctx->cycle.graph);
+      ctx->cycle.exec = nullptr;
+      ctx->cycle.graph = nullptr;
+    }
+    if (!ctx->capture_stream)
+      LQCD_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
+    LQCD_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    // the profiling events (owned by ctx) are recorded by event nodes of the graph
+    lqcd_status st = run_cycle_direct(ctx, b, op, reorth, prof, ctx->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (st != LQCD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "end capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_error(e, "graph instantiate");
+    }
+    ctx->cycle.graph = g;
+    ctx->cycle.exec = ex;
+    ctx->cycle.key = key;
+  }
+  LQCD_CUDA(cudaGraphLaunch(ctx->cycle.exec, s), "graph launch");
+  if (prof->on) prof->used = b.m;
+  return LQCD_OK;
+}
+
+// Accumulate the event times of the steps that ran (j < kmax: later steps were
+// skipped on the device once every rhs had finished its cycle).
+static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n, bool f64, bool reorth) {
+  if (!prof->on) return;
+  for (int j = 0; j < prof->used && j < kmax; ++j) {
+    float a = 0.f, c = 0.f;
+    if (cudaEventElapsedTime(&a, prof->ev[4 * j], prof->ev[4 * j + 1]) == cudaSuccess) {
+      prof->op_ms += a;
+      prof->op_n += 1;
+      prof->op_bytes += op_bytes;
+    }
+    if (cudaEventElapsedTime(&c, prof->ev[4 * j + 2], prof->ev[4 * j + 3]) == cudaSuccess) {
+      prof->gs_ms += c;
+      prof->gs_n += 1;
+      prof->gs_bytes += gs_algorithmic_bytes(n, j + 1, f64, reorth);
+    }
+  }
+  prof->used = 0;
+  cudaGetLastError();
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+// Pinned staging layout used by the solve (host side of the per-rhs scalars).
+struct Staging {
+  double rn2[2 * 256];      // reduced double2 norms (x, y)
+  double beta0[256];
+  double thr[256];
+  int active[256];
+  int kcycle[256];
+};
+
+extern "C" {
+
+lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs, int nvec,
+                               const void* basis, void* w, void* h, void* hnorm, int reorth, void* stream) {
+  if (!ctx) return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: null context");
+  if ((dtype != LQCD_C64 && dtype != LQCD_C128) || nrhs < 1 || nrhs > 256 || nvec < 1 || nvec > 64 || !basis ||
+      !w || !h || !hnorm || (sites != LQCD_SITES_FULL && sites != LQCD_SITES_EVEN && sites != LQCD_SITES_ODD))
+    return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = dtype == LQCD_C128;
+  const int64_t n = (int64_t)packed_elems(ctx, sites, nrhs);
+  BlasPlan plan = blas_plan(n, nrhs, ctx->num_sms);
+  void *partials, *h1, *h2, *hn;
+  const size_t hb = sizeof(double2) * (size_t)(nvec + 1) * nrhs;
+  lqcd_status st = workspace(ctx, "ortho_partials", hb * plan.blocks, &partials);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_h1", hb, &h1);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_h2", hb, &h2);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_hn", hb, &hn);
+  if (st != LQCD_OK) return st;
+  LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, nullptr, false, true, false, partials, h1, nullptr, s),
+            "gs dots");
+  if (reorth) {
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, true, false, partials, h2, nullptr, s),
+              "gs update+dots");
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h2, true, false, true, partials, hn, nullptr, s),
+              "gs update+norm");
+  } else {
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, false, true, partials, hn, nullptr, s),
+              "gs update+norm");
+  }
+  const int q = nvec * nrhs > nrhs ? nvec * nrhs : nrhs;
+  combine_h_kernel<<<(q + 127) / 128, 128, 0, s>>>(nvec, nrhs, (const double2*)h1,
+                                                   reorth ? (const double2*)h2 : nullptr, (const double2*)hn,
+                                                   (double2*)h, (double*)hnorm);
+  LQCD_CUDA(cudaGetLastError(), "combine h");
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const void* b, void* x,
+                       lqcd_solve_stats* stats, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!ctx || !P || !b || !x) return set_error(LQCD_ERR_ARG, "lqcd_solve: null argument");
+  if (!ctx->have_gauge || !ctx->have_blocks)
+    return set_error(LQCD_ERR_STATE, "lqcd_solve: set_gauge and set_clover must be called first");
+  if (nrhs < 1 || nrhs > 64 || P->restart_len < 1 || P->restart_len > 64 || P->max_restarts < 1 ||
+      !(P->tol > 0.0) || (P->op != LQCD_OP_FULL && P->op != LQCD_OP_SCHUR) ||
+      (P->precision != LQCD_C64 && P->precision != LQCD_C128))
+    return set_error(LQCD_ERR_ARG, "lqcd_solve: bad parameters (nrhs 1..64, restart_len 1..64, tol > 0)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool eo = P->op == LQCD_OP_SCHUR;
+  const bool f64_inner = P->precision == LQCD_C128;
+  const int m = P->restart_len;
+  const bool reorth = P->reorth != 0;
+  const double inner_tol = P->inner_tol > 0.0 ? P->inner_tol : (f64_inner ? 0.0 : 1e-5);
+  long long nl = 0;  // kernel launches of this call
+  const int64_t n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
+  const int64_t n_half = n_full / 2;
+  const int64_t n_sys = eo ? n_half : n_full;
+  const size_t full64 = (size_t)n_full * sizeof(double2);
+  lqcd_status st;
+
+  // ---------------- buffers
+  void *b_can = (void*)b, *x_can = x, *b64, *x64, *r64, *t64, *bhat = nullptr, *tmp64 = nullptr;
+  const bool b_host = !is_device_pointer(b), x_host = !is_device_pointer(x);
+  if (b_host && (st = workspace(ctx, "solve_b_can", full64, &b_can)) != LQCD_OK) return st;
+  if (x_host && (st = workspace(ctx, "solve_x_can", full64, &x_can)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_b64", full64, &b64)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_x64", full64, &x64)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_r64", full64, &r64)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_t64", full64, &t64)) != LQCD_OK) return st;
+  if (eo) {
+    if ((st = workspace(ctx, "solve_bhat", (size_t)n_half * sizeof(double2), &bhat)) != LQCD_OK) return st;
+    if ((st = workspace(ctx, "schur_tmp64", (size_t)n_half * sizeof(double2), &tmp64)) != LQCD_OK) return st;
+  }
+  SolveBufs B;
+  B.f64_inner = f64_inner;
+  B.nrhs = nrhs;
+  B.m = m;
+  B.n_sys = n_sys;
+  B.inner_bytes = (size_t)n_sys * (f64_inner ? sizeof(double2) : sizeof(float2));
+  if ((st = workspace(ctx, "solve_basis", B.inner_bytes * (m + 1), &B.basis)) != LQCD_OK) return st;
+  B.tmp_even_in = nullptr;
+  if (eo) {
+    if (f64_inner) B.tmp_even_in = tmp64;
+    else if ((st = workspace(ctx, "schur_tmp32", (size_t)n_half * sizeof(float2), &B.tmp_even_in)) != LQCD_OK)
+      return st;
+  }
+  B.plan = blas_plan(n_sys, nrhs, ctx->num_sms);
+  const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
+  if ((st = workspace(ctx, "solve_partials", hb * B.plan.blocks, &B.partials)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_h1", hb, &B.h1)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_h2", hb, &B.h2)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_hn", hb, &B.hn)) != LQCD_OK) return st;
+  // small per-rhs state, one allocation carved into 256-byte aligned pieces
+  const size_t piece[12] = {sizeof(double2) * (size_t)nrhs * m * (m + 1), sizeof(double) * (size_t)nrhs * m,
+                            sizeof(double2) * (size_t)nrhs * m, sizeof(double2) * (size_t)nrhs * (m + 1),
+                            sizeof(double2) * (size_t)m * nrhs, sizeof(double) * nrhs, sizeof(double) * nrhs,
+                            sizeof(int) * nrhs, sizeof(int) * nrhs, sizeof(int) * nrhs, sizeof(int), sizeof(int)};
+  size_t small_bytes = 0;
+  for (size_t q : piece) small_bytes += (q + 255) & ~(size_t)255;
+  void* small;
+  if ((st = workspace(ctx, "solve_small", small_bytes, &small)) != LQCD_OK) return st;
+  {
+    char* p = (char*)small;
+    int next = 0;
+    auto take = [&]() { void* q = p; p += (piece[next++] + 255) & ~(size_t)255; return q; };
+    B.st.m = m;
+    B.st.nrhs = nrhs;
+    B.st.H = (double2*)take();
+    B.st.cs = (double*)take();
+    B.st.sn = (double2*)take();
+    B.st.gamma = (double2*)take();
+    B.st.y = (double2*)take();
+    B.st.thr = (double*)take();
+    B.st.scale = (double*)take();
+    B.st.active = (int*)take();
+    B.st.done = (int*)take();
+    B.st.k = (int*)take();
+    B.st.all_done = (int*)take();
+    B.st.kmax = (int*)take();
+  }
+  double* d_beta0;
+  if ((st = workspace(ctx, "solve_beta0", sizeof(double) * nrhs, (void**)&d_beta0)) != LQCD_OK) return st;
+  Staging* hs;
+  if ((st = pinned_staging(ctx, sizeof(Staging), (void**)&hs)) != LQCD_OK) return st;
+
+  Profile prof;
+  prof.on = P->profile != 0;
+  if (prof.on) {
+    if (ctx->prof_events.empty()) {
+      ctx->prof_events.resize(4 * 64);
+      for (auto& e : ctx->prof_events) LQCD_CUDA(cudaEventCreate(&e), "event create");
+    }
+    prof.ev = ctx->prof_events;
+  }
+
+  // ---------------- inputs
+  if (b_host) LQCD_CUDA(cudaMemcpyAsync(b_can, b, full64, cudaMemcpyHostToDevice, s), "upload b");
+  if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, b_can, b64, s)) != LQCD_OK) return st;
+  if (P->x0_given) {
+    if (x_host) LQCD_CUDA(cudaMemcpyAsync(x_can, x, full64, cudaMemcpyHostToDevice, s), "upload x0");
+    if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x_can, x64, s)) != LQCD_OK) return st;
+  } else {
+    LQCD_CUDA(cudaMemsetAsync(x64, 0, full64, s), "zero x");
+  }
+  BlasPlan plan_full = blas_plan(n_full, nrhs, ctx->num_sms);
+  void* red_partials;
+  if ((st = workspace(ctx, "solve_partials_full", sizeof(double2) * (size_t)nrhs * plan_full.blocks,
+                      &red_partials)) != LQCD_OK)
+    return st;
+  LQCD_CUDA(launch_norm2(true, plan_full, n_full, b64, red_partials, B.hn, s), "norm b");
+  nl += (P->x0_given ? 2 : 1) + 2 + (eo ? 2 : 0);  // packs, norm + reduction, prepare
+  LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read norm b");
+  LQCD_CUDA(cudaStreamSynchronize(s), "sync");
+  std::vector<double> bnorm(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm[r] = std::sqrt(hs->rn2[2 * r]);
+    if (!std::isfinite(bnorm[r]))
+      return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: right-hand side %d is not finite", r);
+  }
+  void* sys_b = b64;
+  void* sys_x = x64;
+  if (eo) {
+    if ((st = schur_prepare(ctx, true, nrhs, b64, bhat, tmp64, s)) != LQCD_OK) return st;
+    sys_b = bhat;
+    sys_x = (char*)x64 + (size_t)n_half * sizeof(double2);
+  }
+
+  // ---------------- restarts
+  std::vector<int> iters(nrhs, 0);
+  std::vector<double> relres(nrhs, 0.0);
+  const double op_bytes_inner = op_algorithmic_bytes(ctx, P->op, f64_inner, nrhs);
+  int restarts = 0;
+  lqcd_status result = LQCD_NOT_CONVERGED;
+  bool pending_k = false;
+  for (;;) {
+    // true residual r = b - D x in FP64
+    if ((st = apply_operator(ctx, P->op, true, nrhs, sys_x, t64, tmp64, nullptr, s)) != LQCD_OK) return st;
+    LQCD_CUDA(launch_sub_norm(B.plan, n_sys, sys_b, t64, r64, B.partials, B.hn, s), "residual");
+    LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read rn");
+    LQCD_CUDA(cudaStreamSynchronize(s), "sync residual");
+    nl += eo ? 4 : 3;  // FP64 operator + residual kernel + reduction
+    if (pending_k) {
+      int kmax = 0;
+      for (int r = 0; r < nrhs; ++r) {
+        iters[r] += hs->kcycle[r];
+        kmax = std::max(kmax, hs->kcycle[r]);
+      }
+      collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth);
+    }
+    pending_k = false;
+    int n_active = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rn = std::sqrt(hs->rn2[2 * r]);
+      if (!std::isfinite(rn))
+        return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: residual of rhs %d is not finite", r);
+      relres[r] = bnorm[r] > 0.0 ? rn / bnorm[r] : 0.0;
+      const bool act = bnorm[r] > 0.0 && rn > P->tol * bnorm[r];
+      hs->active[r] = act ? 1 : 0;
+      hs->beta0[r] = act ? rn : 1.0;
+      // cycle target: half the tolerance (so the true residual, which the Arnoldi
+      // estimate approximates, lands below tol), or the inner relative reduction
+      double thr = 0.5 * P->tol * bnorm[r];
+      if (inner_tol > 0.0) thr = std::max(thr, inner_tol * rn);
+      hs->thr[r] = thr;
+      n_active += act;
+    }
+    if (n_active == 0) {
+      result = LQCD_OK;
+      break;
+    }
+    if (restarts >= P->max_restarts) break;
+    LQCD_CUDA(cudaMemcpyAsync(B.st.active, hs->active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s), "up");
+    LQCD_CUDA(cudaMemcpyAsync(B.st.thr, hs->thr, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
+    LQCD_CUDA(cudaMemcpyAsync(d_beta0, hs->beta0, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
+    LQCD_CUDA(launch_cycle_init(B.st, d_beta0, s), "cycle init");
+    LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, s), "v0");
+    if ((st = run_cycle(ctx, B, P->op, reorth, P->use_graph != 0, &prof, s)) != LQCD_OK) return st;
+    LQCD_CUDA(launch_backsub(B.st, s), "backsub");
+    LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, s),
+              "update x");
+    // cycle_init, v0, per step (operator + Gram-Schmidt kernels and reductions + givens + scale), backsub, update
+    nl += 4 + (long long)m * ((eo ? 2 : 1) + (reorth ? 6 : 4) + 2);
+    LQCD_CUDA(cudaMemcpyAsync(hs->kcycle, B.st.k, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s), "read k");
+    pending_k = true;
+    ++restarts;
+  }
+
+  // ---------------- finish: reconstruct, final full-operator residual, output
+  if (eo && (st = schur_reconstruct(ctx, true, nrhs, b64, sys_x, x64, s)) != LQCD_OK) return st;
+  if ((st = apply_operator(ctx, LQCD_OP_FULL, true, nrhs, x64, t64, nullptr, nullptr, s)) != LQCD_OK) return st;
+  LQCD_CUDA(launch_sub_norm(plan_full, n_full, b64, t64, r64, red_partials, B.hn, s), "final residual");
+  LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read final");
+  if ((st = lqcd_unpack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x64, x_can, s)) != LQCD_OK) return st;
+  if (x_host) LQCD_CUDA(cudaMemcpyAsync(x, x_can, full64, cudaMemcpyDeviceToHost, s), "download x");
+  LQCD_CUDA(cudaStreamSynchronize(s), "final sync");
+  nl += (eo ? 1 : 0) + 1 + 2 + 1;  // reconstruct, full operator, residual + reduction, unpack
+  double relmax = 0.0;
+  int itmax = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    relres[r] = bnorm[r] > 0.0 ? std::sqrt(hs->rn2[2 * r]) / bnorm[r] : 0.0;
+    relmax = std::max(relmax, relres[r]);
+    itmax = std::max(itmax, iters[r]);
+  }
+  if (stats) {
+    stats->status = result;
+    stats->restarts = restarts;
+    stats->iterations = itmax;
+    stats->relres_max = relmax;
+    stats->op_ms = prof.op_ms;
+    stats->op_launches = prof.op_n;
+    stats->op_bytes = prof.op_bytes;
+    stats->ortho_ms = prof.gs_ms;
+    stats->ortho_launches = prof.gs_n;
+    stats->ortho_bytes = prof.gs_bytes;
+    stats->kernel_launches = nl;
+    if (stats->iters_per_rhs) for (int r = 0; r < nrhs; ++r) stats->iters_per_rhs[r] = iters[r];
+    if (stats->relres_per_rhs) for (int r = 0; r < nrhs; ++r) stats->relres_per_rhs[r] = relres[r];
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (result == LQCD_NOT_CONVERGED)
+    set_error(LQCD_NOT_CONVERGED, "lqcd_solve: max_restarts reached, max relative residual %.3e", relmax);
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+"""CPU checks of the C ABI library: it builds for sm_103a, loads, exports every
+symbol declared in include/lqcd.h, and rejects bad arguments on the host
+(no CUDA compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_05816_gb300 import _build
+    import paper_2601_05816_gb300 as lq
+    _build.build()
+    return lq.load()
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for need in ("lqcd_create", "lqcd_free", "lqcd_set_gauge", "lqcd_set_clover", "lqcd_apply",
+                 "lqcd_apply_packed", "lqcd_solve", "lqcd_schur_prepare", "lqcd_schur_reconstruct",
+                 "lqcd_orthogonalise", "lqcd_pack", "lqcd_unpack"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"liblqcd.so lacks {missing}"
+
+
+def test_host_side_argument_errors(lib):
+    import paper_2601_05816_gb300 as lq
+    h = ctypes.c_void_p()
+    odd = (ctypes.c_int * 4)(4, 4, 3, 4)
+    assert lib.lqcd_create(odd, -1, ctypes.byref(h)) == lq.ERR_ARG
+    assert b"not even" in lib.lqcd_last_error()
+    assert lib.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), 0, ctypes.byref(h)) == lq.ERR_ARG
+    assert lib.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), -1, ctypes.byref(h)) == lq.OK
+    # operator use before the gauge field is set is refused on the host
+    buf = ctypes.c_void_p(16)
+    assert lib.lqcd_apply_packed(h, lq.OP_FULL, lq.C64, 4, buf, buf, None) == lq.ERR_STATE
+    assert lib.lqcd_set_clover(h, 0.1, 1.0, None) == lq.ERR_STATE
+    assert lib.lqcd_packed_bytes(h, lq.C64, lq.SITES_ODD, 3) == 128 * 12 * 3 * 8
+    assert lib.lqcd_packed_bytes(h, 7, lq.SITES_ODD, 3) == 0
+    assert lib.lqcd_site_tile(h, 1) == 16 and lib.lqcd_site_tile(h, 12) == 2 and lib.lqcd_site_tile(h, 16) == 1
+    assert lib.lqcd_status_string(lq.ERR_SINGULAR) == b"singular site block"
+    assert lib.lqcd_free(h) == lq.OK
+    assert lib.lqcd_free(None) == lq.OK

@@ -1,0 +1,240 @@
+"""GPU parity of the operator path (through the C ABI) against the FP64 oracle.
+
+Tolerances (norm-wise relative, per rhs): FP64 1e-12 (the applies are exact
+linear algebra; the two sides differ only in summation order, ~1e-15);
+FP32 5e-6: inputs rounded to FP32 (relative 6e-8) and about a hundred
+accumulated products per output component give an expected relative error of
+~1e-6 for Gaussian inputs, so 5e-6 leaves a factor of a few.
+Layout conversion is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2601_05816_gb300 as lq  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2601_05816_gb300 import _build
+    _build.build()
+    lq.load()
+
+
+TOL = {lq.C128: 1e-12, lq.C64: 5e-6}
+
+_CACHE = {}
+
+
+def setup(dims, kind, eps, m0, c_sw, seed):
+    key = (dims, kind, eps, m0, c_sw, seed)
+    if key not in _CACHE:
+        U = syn.gauge_field(dims, kind, eps, seed=seed)
+        lat = lq.Lattice(dims, time_bc=-1)
+        lat.set_gauge(torch.from_numpy(U).cuda())
+        lat.set_clover(m0, c_sw)
+        C = oracle.clover_term(U, c_sw)
+        A, Ainv = oracle.diag_blocks(U, m0, c_sw)
+        _CACHE[key] = (lat, U, C, A, Ainv)
+    return _CACHE[key]
+
+
+def dev(a, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t if dtype == lq.C128 else t.to(torch.complex64)).cuda()
+
+
+def relerr(got, ref):
+    got = np.asarray(got, dtype=np.complex128).reshape(ref.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return max(np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k]) for k in range(ref.shape[0]))
+
+
+CASES = [
+    # dims, gauge kind, eps, m0, c_sw
+    ((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0),
+    ((4, 4, 4, 4), "haar", 0.0, 0.1, 0.0),
+    ((8, 2, 6, 4), "exp", 0.5, 0.05, 1.3),     # non-cubic: catches stride mistakes
+    ((2, 2, 2, 2), "exp", 0.7, 0.2, 1.0),      # both hops on one site; site tile capped at 8
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_site_blocks_match_oracle(case):
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    V = lat.V
+    out = torch.empty((V, 12, 12), dtype=torch.complex128, device="cuda")
+    for which, ref in ((0, A), (1, Ainv)):
+        lat.export_blocks(which, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(ref.shape)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+@pytest.mark.parametrize("nrhs", [1, 3, 12, 16])
+@pytest.mark.parametrize("sites", [lq.SITES_FULL, lq.SITES_ODD])
+def test_pack_unpack_roundtrip_bit_exact(dtype, nrhs, sites):
+    lat, *_ = setup((8, 2, 6, 4), "exp", 0.5, 0.05, 1.3, 101)
+    n_sites = lat.V if sites == lq.SITES_FULL else lat.V // 2
+    g = torch.Generator(device="cpu").manual_seed(nrhs)
+    src = torch.randn((nrhs, n_sites, 4, 3), dtype=torch.complex128, generator=g)
+    src = src if dtype == lq.C128 else src.to(torch.complex64)
+    src = src.cuda()
+    packed = lat.packed_empty(dtype, sites, nrhs)
+    back = torch.empty_like(src)
+    lat.pack(sites, nrhs, src, packed)
+    lat.unpack(sites, nrhs, packed, back)
+    torch.cuda.synchronize()
+    assert torch.equal(src, back)
+    # spot-check the packed position of (site i, component c, rhs r)
+    S = lat.site_tile(nrhs)
+    p = packed.cpu()
+    s = src.cpu().reshape(nrhs, n_sites, 12)
+    for (i, c, r) in [(0, 0, 0), (n_sites - 1, 11, nrhs - 1), (n_sites // 3, 5, nrhs // 2)]:
+        if sites == lq.SITES_FULL:
+            t, z, y, x = np.unravel_index(i, lat.dims)
+            par = (t + z + y + x) % 2
+            e = par * (lat.V // 2) + i // 2
+        else:
+            e = i
+        idx = ((e // S) * 12 + c) * S * nrhs + (e % S) * nrhs + r
+        assert p[idx] == s[r, i, c]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 13, 16])
+def test_full_operator(case, dtype, nrhs):
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    psi = syn.gaussian_spinors(dims, nrhs, 200 + nrhs)
+    ref = oracle.apply_D(U, psi, m0, C if c_sw else None)
+    d_in = dev(psi, dtype)
+    d_out = torch.empty_like(d_in)
+    lat.apply(lq.OP_FULL, nrhs, d_in, d_out)
+    torch.cuda.synchronize()
+    assert relerr(d_out.cpu().numpy(), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
+@pytest.mark.parametrize("nrhs", [1, 4, 12, 13])
+def test_schur_operator(case, dtype, nrhs):
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    psi_o = oracle.split_parity(syn.gaussian_spinors(dims, nrhs, 300 + nrhs), 1)
+    ref = oracle.apply_schur(U, A, Ainv, psi_o)
+    d_in = dev(psi_o, dtype)
+    d_out = torch.empty_like(d_in)
+    lat.apply(lq.OP_SCHUR, nrhs, d_in, d_out)
+    torch.cuda.synchronize()
+    assert relerr(d_out.cpu().numpy(), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
+def test_schur_prepare_reconstruct(case, dtype):
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    nrhs = 3
+    b = syn.gaussian_spinors(dims, nrhs, 400)
+    x_o = oracle.split_parity(syn.gaussian_spinors(dims, nrhs, 401), 1)
+    b_e, b_o = oracle.split_parity(b, 0), oracle.split_parity(b, 1)
+    ref_bhat = oracle.schur_prepare(U, Ainv, b_e, b_o)
+    ref_xe = oracle.schur_reconstruct(U, Ainv, b_e, x_o)
+    bp = lat.packed_empty(dtype, lq.SITES_FULL, nrhs)
+    lat.pack(lq.SITES_FULL, nrhs, dev(b, dtype), bp)
+    bhat_p = lat.packed_empty(dtype, lq.SITES_ODD, nrhs)
+    lat.schur_prepare(nrhs, bp, bhat_p)
+    bhat = torch.empty((nrhs, lat.V // 2, 4, 3), dtype=bp.dtype, device="cuda")
+    lat.unpack(lq.SITES_ODD, nrhs, bhat_p, bhat)
+    xo_p = lat.packed_empty(dtype, lq.SITES_ODD, nrhs)
+    lat.pack(lq.SITES_ODD, nrhs, dev(x_o, dtype), xo_p)
+    x_p = lat.packed_empty(dtype, lq.SITES_FULL, nrhs)
+    lat.schur_reconstruct(nrhs, bp, xo_p, x_p)
+    x = torch.empty((nrhs, lat.V, 4, 3), dtype=bp.dtype, device="cuda")
+    lat.unpack(lq.SITES_FULL, nrhs, x_p, x)
+    torch.cuda.synchronize()
+    assert relerr(bhat.cpu().numpy(), ref_bhat) < TOL[dtype]
+    xfull = x.cpu().numpy().reshape((nrhs,) + dims + (4, 3))
+    assert relerr(oracle.split_parity(xfull, 0), ref_xe) < TOL[dtype]
+    assert np.array_equal(oracle.split_parity(xfull, 1).astype(np.complex128),
+                          x_o.astype(xfull.dtype).astype(np.complex128))
+
+
+@pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
+@pytest.mark.parametrize("nvec,nrhs,reorth", [(1, 1, True), (5, 3, True), (17, 12, False), (32, 16, True)])
+def test_orthogonalise_matches_projection(dtype, nvec, nrhs, reorth):
+    """h = V^H w and w' = (1 - V V^H) w per rhs for an orthonormal basis (numpy QR)."""
+    lat, *_ = setup((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0, 101)
+    n_sites = lat.V // 2
+    rng = np.random.default_rng(nvec * 100 + nrhs)
+    N = n_sites * 12
+    Vb = np.empty((nvec, nrhs, N), complex)
+    for r in range(nrhs):
+        Z = rng.standard_normal((N, nvec)) + 1j * rng.standard_normal((N, nvec))
+        Q, _ = np.linalg.qr(Z)
+        Vb[:, r, :] = Q.T
+    w = rng.standard_normal((nrhs, N)) + 1j * rng.standard_normal((nrhs, N))
+    if dtype == lq.C64:   # reference on the FP32-rounded inputs
+        Vb = Vb.astype(np.complex64).astype(complex)
+        w = w.astype(np.complex64).astype(complex)
+    h_ref = np.einsum("irn,rn->ir", Vb.conj(), w)
+    w_ref = w - np.einsum("irn,ir->rn", Vb, h_ref)
+    basis = torch.cat([lat.packed_empty(dtype, lq.SITES_ODD, nrhs) for _ in range(nvec)])
+    nb = basis.numel() // nvec
+    for i in range(nvec):
+        lat.pack(lq.SITES_ODD, nrhs, dev(Vb[i].reshape(nrhs, n_sites, 4, 3), dtype), basis[i * nb:(i + 1) * nb])
+    wp = lat.packed_empty(dtype, lq.SITES_ODD, nrhs)
+    lat.pack(lq.SITES_ODD, nrhs, dev(w.reshape(nrhs, n_sites, 4, 3), dtype), wp)
+    h = torch.empty((nvec, nrhs), dtype=torch.complex128, device="cuda")
+    hn = torch.empty(nrhs, dtype=torch.float64, device="cuda")
+    lat.orthogonalise(lq.SITES_ODD, nrhs, nvec, basis, wp, h, hn, reorth=reorth)
+    wout = torch.empty((nrhs, n_sites, 4, 3), dtype=wp.dtype, device="cuda")
+    lat.unpack(lq.SITES_ODD, nrhs, wp, wout)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == lq.C128 else 2e-5
+    assert np.max(np.abs(h.cpu().numpy() - h_ref)) < tol * np.max(np.abs(h_ref)) * 10
+    got_w = wout.cpu().numpy().reshape(nrhs, N)
+    assert relerr(got_w, w_ref) < (1e-12 if dtype == lq.C128 else 1e-5)
+    assert np.allclose(hn.cpu().numpy(), np.linalg.norm(got_w, axis=1), rtol=1e-6 if dtype == lq.C64 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+def test_operator_sweep_lattice_sampled_rhs(dtype):
+    """16^3 x 32, Wilson-clover, nrhs = 16 in the launch configuration the bench
+    times; rhs 0 and 15 checked against the oracle (rhs are independent)."""
+    dims = (32, 16, 16, 16)
+    m0, c_sw, nrhs = -0.2, 1.0, 16
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1 * 1000 + 1)
+    lat = lq.Lattice(dims, time_bc=-1)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    psi = syn.gaussian_spinors(dims, nrhs, 1 * 1000 + 2)
+    psi_o = oracle.split_parity(psi, 1)
+    sample = [0, nrhs - 1]
+    A, Ainv = oracle.diag_blocks(U, m0, c_sw)
+    ref_s = oracle.apply_schur(U, A, Ainv, psi_o[sample])
+    ref_f = oracle.apply_D(U, psi[sample], m0, oracle.clover_term(U, c_sw))
+    for op, src, ref, sites in ((lq.OP_SCHUR, psi_o, ref_s, lq.SITES_ODD), (lq.OP_FULL, psi, ref_f, lq.SITES_FULL)):
+        d_in = dev(src, dtype)
+        pin = lat.packed_empty(dtype, sites, nrhs)
+        pout = lat.packed_empty(dtype, sites, nrhs)
+        lat.pack(sites, nrhs, d_in, pin)
+        lat.apply_packed(op, nrhs, pin, pout)
+        out = torch.empty_like(d_in)
+        lat.unpack(sites, nrhs, pout, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()[sample]
+        assert relerr(got, ref) < TOL[dtype]
+    lat.close()

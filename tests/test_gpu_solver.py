@@ -1,0 +1,134 @@
+"""GPU batched GMRES (through lqcd_solve) checked against the FP64 oracle.
+
+A solve is accepted when the ORACLE's operator applied to the GPU solution
+gives ||b - D x|| / ||b|| <= tol for every rhs (the solution itself is unique,
+the iterates are not: the GPU uses CGS2 where the oracle uses MGS). The GPU
+solution is also compared with the oracle's solve; their difference is bounded
+by about cond(D) * tol, checked loosely.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2601_05816_gb300 as lq  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2601_05816_gb300 import _build
+    _build.build()
+    lq.load()
+
+
+def oracle_relres(U, m0, c_sw, b, x):
+    C = oracle.clover_term(U, c_sw) if c_sw else None
+    r = b - oracle.apply_D(U, x, m0, C)
+    return np.array([np.linalg.norm(r[k]) / np.linalg.norm(b[k]) for k in range(b.shape[0])])
+
+
+@pytest.mark.parametrize("op", [lq.OP_FULL, lq.OP_SCHUR])
+@pytest.mark.parametrize("precision", [lq.C128, lq.C64])
+def test_haar_4x4_wilson_solve(op, precision):
+    """4^4, Wilson, m0 = 0.1, Haar links, one rhs, GMRES(30) to 1e-10, full and odd-even."""
+    dims = (4, 4, 4, 4)
+    U = syn.gauge_field(dims, "haar", seed=0)
+    b = syn.gaussian_spinors(dims, 1, 1)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(U)
+    lat.set_clover(0.1, 0.0)
+    x = np.zeros_like(b)
+    res = lat.solve(b, x, 1, op=op, precision=precision, restart_len=30, tol=1e-10, use_graph=False)
+    assert res.status == lq.OK
+    rel = oracle_relres(U, 0.1, 0.0, b, x)
+    assert np.all(rel <= 1e-10), rel
+    assert res.relres_max <= 1e-10
+    xo, _ = oracle.solve_full(U, None, 0.1, b, tol=1e-12, m=30, max_restarts=50)
+    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+    lat.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_clover_multi_rhs_eo_mixed(use_graph):
+    """8^4 Wilson-clover (eps 0.3, m0 = -0.2), 5 rhs (odd count), mixed precision, odd-even."""
+    dims = (8, 8, 8, 8)
+    m0, c_sw = -0.2, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1001)
+    b = syn.gaussian_spinors(dims, 5, 1002)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    res = lat.solve(torch.from_numpy(b).cuda(), x, 5, op=lq.OP_SCHUR, precision=lq.C64, restart_len=32,
+                    tol=1e-10, use_graph=use_graph)
+    torch.cuda.synchronize()
+    assert res.status == lq.OK, res
+    rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
+    assert np.all(rel <= 1e-10), rel
+    assert np.allclose(rel, res.relres_per_rhs, rtol=1e-3, atol=1e-13)
+    lat.close()
+
+
+def test_fp64_and_mixed_agree_and_eo_needs_fewer_iterations():
+    dims = (8, 4, 4, 8)
+    m0, c_sw = 0.0, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=77)
+    b = syn.gaussian_spinors(dims, 2, 78)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(U)
+    lat.set_clover(m0, c_sw)
+    out = {}
+    for op in (lq.OP_FULL, lq.OP_SCHUR):
+        for prec in (lq.C128, lq.C64):
+            x = np.zeros_like(b)
+            res = lat.solve(b, x, 2, op=op, precision=prec, restart_len=16, tol=1e-10)
+            assert res.status == lq.OK
+            assert np.all(oracle_relres(U, m0, c_sw, b, x) <= 1e-10)
+            out[(op, prec)] = (x, res)
+    xs = [v[0] for v in out.values()]
+    for x in xs[1:]:
+        assert np.linalg.norm(x - xs[0]) <= 1e-7 * np.linalg.norm(xs[0])
+    assert out[(lq.OP_SCHUR, lq.C128)][1].iterations < out[(lq.OP_FULL, lq.C128)][1].iterations
+    lat.close()
+
+
+def test_initial_guess_and_zero_rhs():
+    """x0 = the solution converges with no iteration; a zero rhs gives x = 0."""
+    dims = (4, 4, 4, 4)
+    U = syn.gauge_field(dims, "exp", 0.3, seed=5)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(U)
+    lat.set_clover(0.1, 1.0)
+    b = syn.gaussian_spinors(dims, 2, 6)
+    b[1] = 0
+    x = np.zeros_like(b)
+    res = lat.solve(b, x, 2, op=lq.OP_SCHUR, precision=lq.C128, restart_len=20, tol=1e-11)
+    assert res.status == lq.OK and np.all(x[1] == 0)
+    x2 = x.copy()
+    res2 = lat.solve(b, x2, 2, op=lq.OP_SCHUR, precision=lq.C128, restart_len=20, tol=1e-10, x0_given=True)
+    assert res2.status == lq.OK and res2.iterations == 0 and res2.restarts == 0
+    lat.close()
+
+
+def test_not_converged_and_nonfinite_status():
+    dims = (4, 4, 4, 4)
+    U = syn.gauge_field(dims, "exp", 0.3, seed=5)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(U)
+    lat.set_clover(-0.2, 1.0)
+    b = syn.gaussian_spinors(dims, 1, 6)
+    x = np.zeros_like(b)
+    res = lat.solve(b, x, 1, op=lq.OP_FULL, precision=lq.C128, restart_len=2, max_restarts=1, tol=1e-12)
+    assert res.status == lq.NOT_CONVERGED and res.relres_max > 1e-12
+    b[0, 0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(lq.LqcdError) as ei:
+        lat.solve(b, x, 1, op=lq.OP_FULL, precision=lq.C128)
+    assert ei.value.status == lq.ERR_NONFINITE
+    lat.close()
