@@ -282,10 +282,12 @@ static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bo
 
 static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reorth, bool use_graph,
                              Profile* prof, cudaStream_t s) {
-  if (!use_graph) return run_cycle_direct(ctx, b, op, reorth, prof, s);
+  // CUDA events recorded inside a graph do not time its kernel nodes, so a
+  // profiled cycle is launched kernel by kernel.
+  if (!use_graph || prof->on) return run_cycle_direct(ctx, b, op, reorth, prof, s);
   char key[256];
-  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%d/%p/%p/%p/%lld", op, (int)b.f64_inner, b.nrhs, b.m, (int)reorth,
-           (int)prof->on, b.basis, b.partials, (void*)b.st.H, (long long)b.n_sys);
+  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%p/%p/%p/%lld", op, (int)b.f64_inner, b.nrhs, b.m, (int)reorth,
+           b.basis, b.partials, (void*)b.st.H, (long long)b.n_sys);
   if (ctx->cycle.exec == nullptr || ctx->cycle.key != key) {
     if (ctx->cycle.exec) {
       cudaGraphExecDestroy(ctx->cycle.exec);
@@ -296,8 +298,8 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
     if (!ctx->capture_stream)
       LQCD_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking), "capture stream");
     LQCD_CUDA(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    // the profiling events (owned by ctx) are recorded by event nodes of the graph
-    lqcd_status st = run_cycle_direct(ctx, b, op, reorth, prof, ctx->capture_stream);
+    Profile none;
+    lqcd_status st = run_cycle_direct(ctx, b, op, reorth, &none, ctx->capture_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
     if (st != LQCD_OK) {
@@ -316,7 +318,6 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
     ctx->cycle.key = key;
   }
   LQCD_CUDA(cudaGraphLaunch(ctx->cycle.exec, s), "graph launch");
-  if (prof->on) prof->used = b.m;
   return LQCD_OK;
 }
 
