@@ -43,6 +43,11 @@ WORKLOADS = {
                   c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, restart=32, tol=1e-10),
     "solve-large": dict(name="eo-gmres32-mixed 32^3x64 clover nrhs=12", dims=(64, 32, 32, 32), eps=0.25, m0=-0.3,
                         c_sw=1.0, nrhs=12, gauge_seed=2000, rhs_seed=2001, restart=32, tol=1e-10),
+    # single-kernel workloads (one step = one launch group), also the small cases for ncu captures
+    "apply": dict(name="schur-apply c64 16^3x32 clover nrhs=16", dims=(32, 16, 16, 16), eps=0.3, m0=-0.2,
+                  c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, kind="apply"),
+    "ortho": dict(name="cgs2-step c64 16^3x32 odd sites nrhs=16 nvec=16", dims=(32, 16, 16, 16), eps=0.3,
+                  m0=-0.2, c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, kind="ortho", nvec=16),
 }
 
 
@@ -132,14 +137,25 @@ def barrier(world):
         dist.barrier()
 
 
-def allreduce_max(world, x):
+def allreduce_max(world, x, device="cuda"):
+    """Max over ranks of a host float (the timed region's length)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_rhs_seed(base_seed: int, rank: int) -> int:
+    """Each rank solves its own batch of sources (weak scaling over independent rhs)."""
+    return base_seed + 7919 * rank
+
+
+def aggregate_throughput(world: int, units_per_rank_step: float, steps: int, t_max: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank_step * steps / t_max
 
 
 # ------------------------------------------------------------------ oracle (CPU) arm
@@ -227,6 +243,82 @@ def dslash_point(lat, lq, torch, dims, nrhs, dtype, op, reps, flush):
     return t, nbytes, units
 
 
+def run_kernel_workload(args, w):
+    """One step = one odd-even Schur apply (c64) or one CGS2 Gram-Schmidt step (c64)."""
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2601_05816_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    import paper_2601_05816_gb300 as lq
+    import synthetic as syn
+    lq.load()
+    dims, nrhs = w["dims"], w["nrhs"]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U = syn.gauge_field(dims, "exp", w["eps"], seed=w["gauge_seed"])
+    lat = lq.Lattice(dims, time_bc=-1)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(w["m0"], w["c_sw"])
+    peak, peak_kind = measured_peaks()
+    g = torch.Generator(device="cuda").manual_seed(7 + rank)
+    if w["kind"] == "apply":
+        pin = lat.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
+        pin.copy_(torch.randn(pin.shape, dtype=pin.dtype, device="cuda", generator=g))
+        pout = torch.empty_like(pin)
+
+        def step():
+            lat.apply_packed(lq.OP_SCHUR, nrhs, pin, pout)
+        nbytes = (V // 2) * (120 * nrhs + 432) * 4
+        launches = 2
+        kernel = "dslash_kernel<float,2> (Schur passes A + B)"
+    else:
+        nvec = w["nvec"]
+        n = (V // 2) * 12 * nrhs
+        basis = torch.randn(nvec * n, dtype=torch.complex64, device="cuda", generator=g)
+        wv = torch.randn(n, dtype=torch.complex64, device="cuda", generator=g)
+        h = torch.empty((nvec, nrhs), dtype=torch.complex128, device="cuda")
+        hn = torch.empty(nrhs, dtype=torch.float64, device="cuda")
+
+        def step():
+            lat.orthogonalise(lq.SITES_ODD, nrhs, nvec, basis, wv, h, hn, reorth=True)
+        nbytes = n * 8 * ((nvec + 1) + 2 * (nvec + 2))
+        launches = 7
+        kernel = "gs_pass_kernel<float2> (CGS2 step: dots, update+dots, update+norm, 3 reductions)"
+    for _ in range(args.warmup):
+        step()
+    s = torch.cuda.current_stream()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(world)
+    t_local = e0.elapsed_time(e1) * 1e-3
+    t = allreduce_max(world, t_local)
+    units = (V // 2) * nrhs
+    achieved = nbytes * args.steps / t_local / 1e9
+    line = {"metric": METRIC, "value": world * units * args.steps / t, "unit": "site·rhs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": w["name"], "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                         "bytes_per_step": nbytes},
+            "clocks": clk.summary(), "gpu_launches": launches * args.steps}
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -242,7 +334,7 @@ def run_gpu(args, w):
     dims, nrhs = w["dims"], w["nrhs"]
     V = dims[0] * dims[1] * dims[2] * dims[3]
     U = syn.gauge_field(dims, "exp", w["eps"], seed=w["gauge_seed"])
-    b = syn.gaussian_spinors(dims, nrhs, w["rhs_seed"] + 7919 * rank)
+    b = syn.gaussian_spinors(dims, nrhs, rank_rhs_seed(w["rhs_seed"], rank))
     U_d = torch.from_numpy(U).cuda()
     b_d = torch.from_numpy(b).cuda()
     x_d = torch.zeros_like(b_d)
@@ -275,7 +367,7 @@ def run_gpu(args, w):
         barrier(world)
     t_local = e0.elapsed_time(e1) * 1e-3
     t = allreduce_max(world, t_local)
-    value = world * V * nrhs * args.steps / t
+    value = aggregate_throughput(world, V * nrhs, args.steps, t)
     for r in results:
         if r.status != lq.OK or r.relres_max > w["tol"]:
             raise SystemExit(f"solve did not converge: {r}")
@@ -400,6 +492,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+    elif w.get("kind") in ("apply", "ortho"):
+        run_kernel_workload(args, w)
     else:
         run_gpu(args, w)
 
