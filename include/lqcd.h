@@ -210,6 +210,30 @@ typedef struct {
 lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* params, int nrhs,
                        const void* b, void* x, lqcd_solve_stats* stats, void* stream);
 
+/* Allocation-free Schur apply. The paper has no counterpart: this entry point
+ * exists for callers that cannot let the library allocate device memory while
+ * they run -- applications whose own pool allocator has already reserved almost
+ * all of the GPU's memory (a cudaMalloc from the library would fail), that must
+ * know their full device-memory footprint up front, or whose latency-critical
+ * loops cannot accept the synchronisation a cudaMalloc/cudaFree may cause.
+ * It computes exactly what lqcd_apply_packed(ctx, LQCD_OP_SCHUR, ...) computes
+ * (same arguments, packed odd-site blocks in/out, same kernels), but keeps the
+ * intermediate A_ee^{-1} D_eo psi_o in a fixed device array of
+ * lqcd_noalloc_scratch_bytes() bytes (64 MiB) that every GPU loading the library
+ * holds until the process exits, and it calls no cudaMalloc, cudaFree or other
+ * allocating routine. Requires V/2 * 12 * nrhs * sizeof(complex) <= that size;
+ * larger requests return LQCD_ERR_ARG with a message and do nothing.
+ * The first call on each device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's contents
+ * (every call overwrites all it reads): calls that overlap on the GPU, e.g. on
+ * two streams at once, race and give wrong results. Requires set_gauge and
+ * set_clover (which allocate, at set-up). */
+lqcd_status lqcd_apply_schur_noalloc(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
+                                     const void* in, void* out, void* stream);
+/* Size in bytes of the fixed scratch array used by lqcd_apply_schur_noalloc. */
+size_t lqcd_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif
