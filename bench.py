@@ -263,7 +263,11 @@ def run_kernel_workload(args, w):
     lat.set_clover(w["m0"], w["c_sw"])
     peak, peak_kind = measured_peaks()
     g = torch.Generator(device="cuda").manual_seed(7 + rank)
+    tuning = None
     if w["kind"] == "apply":
+        tuning = lat.tune(lq.C64, nrhs, reps=5)
+        if args.variant >= 0:
+            lat.set_kernel_variant(lq.C64, nrhs, lq.OP_SCHUR, args.variant)
         pin = lat.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
         pin.copy_(torch.randn(pin.shape, dtype=pin.dtype, device="cuda", generator=g))
         pout = torch.empty_like(pin)
@@ -311,6 +315,9 @@ def run_kernel_workload(args, w):
                          "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                          "bytes_per_step": nbytes},
             "clocks": clk.summary(), "gpu_launches": launches * args.steps}
+    if tuning is not None:
+        line["tuning"] = {"variant_ms_full_schur": tuning,
+                          "chosen_schur": lat.kernel_variant(lq.C64, nrhs, lq.OP_SCHUR)}
     lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -342,6 +349,13 @@ def run_gpu(args, w):
     peak, peak_kind = measured_peaks()
     solve_kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=w["restart"], tol=w["tol"], max_restarts=500,
                     use_graph=True, profile=True)
+
+    # set-up: autotune the hopping kernel for the inner (FP32) and outer (FP64) operators
+    lat.set_gauge(U_d)
+    lat.set_clover(w["m0"], w["c_sw"])
+    tuning = {"c64": lat.tune(lq.C64, nrhs, reps=5), "c128": lat.tune(lq.C128, nrhs, reps=3)}
+    chosen = {k: [lat.kernel_variant(d, nrhs, op) for op in (lq.OP_FULL, lq.OP_SCHUR)]
+              for k, d in (("c64", lq.C64), ("c128", lq.C128))}
 
     def step():
         lat.set_gauge(U_d)
@@ -403,7 +417,8 @@ def run_gpu(args, w):
             "solve": {"iterations": [r.iterations for r in results], "restarts": [r.restarts for r in results],
                       "relres_max": max(r.relres_max for r in results),
                       "seconds_host": [r.seconds for r in results]},
-            "gpu_launches": int(sum(r.kernel_launches for r in results) + args.steps * 5)}
+            "gpu_launches": int(sum(r.kernel_launches for r in results) + args.steps * 5),
+            "tuning": {"variant_ms_full_schur": tuning, "chosen_full_schur": chosen}}
 
     if rank == 0 and not args.skip_extras:
         # operator sweep (dslash GB/s vs HBM roofline), L2 flushed between applies
@@ -415,9 +430,12 @@ def run_gpu(args, w):
         for nr in nr_list:
             for dt in (lq.C64, lq.C128):
                 for op in (lq.OP_SCHUR, lq.OP_FULL):
+                    if op == lq.OP_SCHUR:
+                        lat.tune(dt, nr, reps=3)
                     tt, nb, units = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
                     sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
                                   "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
+                                  "variant": lat.kernel_variant(dt, nr, op),
                                   "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
                                   "site_rhs_per_s": units / tt})
         del flush
@@ -433,9 +451,13 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         mixed_s = statistics.mean(r.seconds for r in results)
+        x_d.zero_()
+        rg = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, profile=False))
+        torch.cuda.synchronize()
         line["gmres"] = {"fp64_s": t64, "mixed_s": mixed_s, "speedup": t64 / mixed_s,
                          "fp64_iterations": r64.iterations, "mixed_iterations": results[-1].iterations,
                          "fp64_relres": r64.relres_max, "mixed_relres": results[-1].relres_max,
+                         "mixed_graph_s": rg.seconds,
                          "note": "host wall time of one synchronised solve (step includes set_gauge/set_clover)"}
         # end to end through the C ABI with pinned host buffers
         U_h = torch.from_numpy(U).pin_memory()
@@ -488,6 +510,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ref-sample-iters", type=int, default=4)
     ap.add_argument("--ref-iterations", type=int, default=300)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -144,6 +144,26 @@ lqcd_status lqcd_apply_packed(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nr
 lqcd_status lqcd_apply(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs,
                        const void* in, void* out, void* stream);
 
+/* Autotuner (not in the paper): times every launch variant of the hopping kernel
+ * -- rhs per thread, threads per CTA, minimum resident CTAs (register cap) -- for
+ * the full and the Schur operator at this (dtype, nrhs) on library workspace
+ * (its contents are arbitrary), and keeps the fastest for every later apply and
+ * solve on this context. reps: timed launches per variant (median kept).
+ * times_ms: optional host array of 2 * n entries receiving, for variant v,
+ * [2v] = full and [2v+1] = Schur median milliseconds (NaN where the variant does
+ * not fit nrhs); n_variants: optional, receives n. Synchronises `stream`. */
+lqcd_status lqcd_tune(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, int reps, double* times_ms,
+                      int* n_variants, void* stream);
+
+/* Tuning cache access: the number of hopping-kernel launch variants for a dtype;
+ * the variant used for (dtype, nrhs, op) on this context (the tuned one, else the
+ * default; -2 on bad arguments); and an explicit choice (e.g. restored from a
+ * saved tuning cache; -1 restores the default). LQCD_ERR_ARG if the variant does
+ * not fit nrhs (rhs per thread must divide nrhs). No GPU work. */
+int lqcd_kernel_variant_count(lqcd_dtype dtype);
+int lqcd_get_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op);
+lqcd_status lqcd_set_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op, int variant);
+
 /* Odd-even source preparation and solution reconstruction (Sec. III-A-2),
  * packed layout, full-lattice blocks hold even then odd sites:
  *   prepare:     bhat_o = b_o - D_oe A_ee^{-1} b_e          (b full, bhat_o odd)

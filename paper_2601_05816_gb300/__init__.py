@@ -71,6 +71,10 @@ _SIGS = {
     "lqcd_schur_reconstruct": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP]),
     "lqcd_orthogonalise": (_I, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "lqcd_solve": (_I, [_VP, ctypes.POINTER(SolveParams), _I, _VP, _VP, ctypes.POINTER(SolveStats), _VP]),
+    "lqcd_tune": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _VP]),
+    "lqcd_kernel_variant_count": (_I, [_I]),
+    "lqcd_get_kernel_variant": (_I, [_VP, _I, _I, _I]),
+    "lqcd_set_kernel_variant": (_I, [_VP, _I, _I, _I, _I]),
 }
 
 
@@ -227,6 +231,42 @@ class Lattice:
         _check(self._lib.lqcd_orthogonalise(self._h, _dtype_code(w), int(sites), int(nrhs), int(nvec),
                                             _ptr(basis), _ptr(w), _ptr(h), _ptr(hnorm), int(bool(reorth)),
                                             _stream(stream)), "lqcd_orthogonalise")
+
+    def tune(self, dtype: int, nrhs: int, reps: int = 5, stream=None):
+        """Autotune the hopping-kernel variant for (dtype, nrhs); returns [(full_ms, schur_ms)] per variant."""
+        times = (ctypes.c_double * 64)()
+        n = ctypes.c_int(0)
+        _check(self._lib.lqcd_tune(self._h, int(dtype), int(nrhs), int(reps), times, ctypes.byref(n),
+                                   _stream(stream)), "lqcd_tune")
+        return [(times[2 * v], times[2 * v + 1]) for v in range(n.value)]
+
+    def kernel_variant(self, dtype: int, nrhs: int, op: int) -> int:
+        return int(self._lib.lqcd_get_kernel_variant(self._h, int(dtype), int(nrhs), int(op)))
+
+    def set_kernel_variant(self, dtype: int, nrhs: int, op: int, variant: int):
+        _check(self._lib.lqcd_set_kernel_variant(self._h, int(dtype), int(nrhs), int(op), int(variant)),
+               "lqcd_set_kernel_variant")
+
+    def save_tuning(self, path: str, keys):
+        """Write the chosen variants for keys = [(dtype, nrhs, op), ...] to a JSON cache."""
+        import json
+        data = {f"{d},{n},{o}": self.kernel_variant(d, n, o) for (d, n, o) in keys}
+        with open(path, "w") as f:
+            json.dump({"dims": list(self.dims), "variants": data}, f, indent=1)
+
+    def load_tuning(self, path: str) -> bool:
+        """Restore variants from a JSON cache written for the same lattice; False if absent or for other dims."""
+        import json
+        if not os.path.exists(path):
+            return False
+        with open(path) as f:
+            data = json.load(f)
+        if tuple(data.get("dims", ())) != self.dims:
+            return False
+        for key, v in data["variants"].items():
+            d, n, o = (int(t) for t in key.split(","))
+            self.set_kernel_variant(d, n, o, int(v))
+        return True
 
     def solve(self, b, x, nrhs: int, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
               max_restarts: int = 200, tol: float = 1e-10, inner_tol: float = 0.0, x0_given: bool = False,

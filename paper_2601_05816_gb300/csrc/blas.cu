@@ -20,6 +20,14 @@ BlasPlan blas_plan(int64_t n, int nrhs, int num_sms) {
   int64_t want = (n + p.threads - 1) / p.threads;
   int64_t cap = 2 * (int64_t)num_sms;
   p.blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+  // the warp-split Gram-Schmidt kernel needs nrhs <= 32 (one rhs per lane)
+  p.split = nrhs <= 32 ? 1 : 0;
+  if (p.split) {
+    const int64_t rows_per_tile = (32 / nrhs) * 4;
+    const int64_t tiles = (n / nrhs + rows_per_tile - 1) / rows_per_tile;
+    const int64_t scap = 4 * (int64_t)num_sms;
+    p.blocks = (int)(tiles < scap ? (tiles < 1 ? 1 : tiles) : scap);
+  }
   return p;
 }
 
@@ -87,8 +95,8 @@ static cudaError_t launch_reduce(int nblk, int nq, const void* partials, void* o
 template <typename C, int NVB, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(256)
 gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64_t vstride,
-               C* __restrict__ w, const double2* __restrict__ coef, double2* __restrict__ partials,
-               const int* skip) {
+               C* __restrict__ w, const double2* __restrict__ coef, const double* __restrict__ oscale,
+               double2* __restrict__ partials, const int* skip) {
   using Real = typename RealOf<C>::T;
   if (skip != nullptr && *skip != 0) return;
   const int tid = threadIdx.x;
@@ -104,6 +112,7 @@ gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64
     }
   }
   Real nn = 0;
+  const Real o_scale = (UPDATE && oscale != nullptr) ? (Real)oscale[r] : (Real)1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + tid; e < n; e += stride) {
     C wv = w[e];
@@ -119,7 +128,7 @@ gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64
           wv.y -= cr[i] * v[i].y + ci[i] * v[i].x;
         }
       }
-      w[e] = wv;
+      w[e] = C{wv.x * o_scale, wv.y * o_scale};
       if (DOTS) {
 #pragma unroll
         for (int i = 0; i < NVB; ++i) {
@@ -154,16 +163,177 @@ gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64
   block_reduce_slots<NVB + 1>(vr, vi, nvec + 1, nrhs, partials);
 }
 
+// Warp-split Gram-Schmidt pass (nrhs <= 32). The block vector is viewed as rows of
+// nrhs elements (the packed layout puts the rhs innermost); a warp covers
+// H = 32 / nrhs rows at once, so every lane keeps one rhs. All eight warps of a
+// CTA walk the same element tiles of 32 * U "slots", and warp k owns the basis
+// vectors i = k, k + 8, ...: its loads of those vectors stay in registers. Per
+// tile, the first 32 * U threads ("slot threads", one per tile element) load w;
+// for an update each warp puts its partial sum_i c_i v_i in shared memory and the
+// slot threads form w - sum (one fixed summation order) and store it; the
+// updated tile goes through shared memory to every warp for the dot products.
+// Registers stay low (several CTAs per SM) and each lane keeps NVW * U vector
+// loads in flight.
+template <typename C, int NVW, int U, bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(256)
+gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64_t vstride,
+                C* __restrict__ w, const double2* __restrict__ coef, const double* __restrict__ oscale,
+                double2* __restrict__ partials, const int* skip) {
+  using Real = typename RealOf<C>::T;
+  static_assert(32 * U <= 256, "one slot thread per tile element");
+  if (skip != nullptr && *skip != 0) return;
+  __shared__ C part[8][32 * U];
+  __shared__ C wsm[2][32 * U];
+  __shared__ double2 red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = 32 / nrhs;
+  const int r = lane % nrhs;
+  const int hrow = lane / nrhs;
+  const bool lane_on = hrow < H;
+  const int64_t Q = n / nrhs;
+  const int64_t tile_rows = (int64_t)H * U;
+  // slot thread: tile element s = threadIdx.x = u * 32 + l, row offset l / nrhs + H u, rhs l % nrhs
+  const int slot = threadIdx.x;
+  const bool is_slot = slot < 32 * U;
+  const int s_l = slot & 31, s_u = slot >> 5;
+  const bool s_on = is_slot && (s_l / nrhs) < H;
+  // optional per-rhs factor applied to the updated w before it is stored
+  const Real s_scale = (UPDATE && oscale != nullptr && s_on) ? (Real)oscale[s_l % nrhs] : (Real)1;
+  Real cr[NVW], ci[NVW], ar[NVW], ai[NVW];
+#pragma unroll
+  for (int k = 0; k < NVW; ++k) {
+    cr[k] = 0; ci[k] = 0; ar[k] = 0; ai[k] = 0;
+    const int i = warp + 8 * k;
+    if (UPDATE && lane_on && i < nvec) {
+      const double2 c = coef[(int64_t)i * nrhs + r];
+      cr[k] = (Real)c.x;
+      ci[k] = (Real)c.y;
+    }
+  }
+  Real nn = 0;
+  int parity = 0;
+  for (int64_t t = blockIdx.x; t * tile_rows < Q; t += gridDim.x, parity ^= 1) {
+    const int64_t row0 = t * tile_rows;
+    // slot thread: its element of w
+    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
+    const bool s_ok = s_on && s_row < Q;
+    const int64_t s_e = s_row * nrhs + (s_l % nrhs);
+    C w_old = C{0, 0};
+    if (s_ok) w_old = w[s_e];
+    // warp: its basis vectors on the tile
+    C v[NVW][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t row = row0 + hrow + (int64_t)H * u;
+      const bool ok = lane_on && row < Q;
+      const int64_t e = row * nrhs + r;
+#pragma unroll
+      for (int k = 0; k < NVW; ++k) {
+        const int i = warp + 8 * k;
+        v[k][u] = (i < nvec && ok) ? __ldg(basis + i * vstride + e) : C{0, 0};
+      }
+    }
+    if (UPDATE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        Real pr = 0, pi = 0;
+#pragma unroll
+        for (int k = 0; k < NVW; ++k) {
+          pr += cr[k] * v[k][u].x - ci[k] * v[k][u].y;
+          pi += cr[k] * v[k][u].y + ci[k] * v[k][u].x;
+        }
+        part[warp][u * 32 + lane] = C{pr, pi};
+      }
+      __syncthreads();
+      if (is_slot) {
+        Real sr = 0, si = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const C pq = part[q][slot];
+          sr += pq.x;
+          si += pq.y;
+        }
+        const C w_new = C{w_old.x - sr, w_old.y - si};
+        if (s_ok) w[s_e] = C{w_new.x * s_scale, w_new.y * s_scale};
+        wsm[parity][slot] = w_new;
+        if (NORM) nn += w_new.x * w_new.x + w_new.y * w_new.y;
+      }
+    } else if (is_slot) {
+      wsm[parity][slot] = w_old;
+      if (NORM) nn += w_old.x * w_old.x + w_old.y * w_old.y;
+    }
+    __syncthreads();
+    if (DOTS) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const C wv = wsm[parity][u * 32 + lane];
+#pragma unroll
+        for (int k = 0; k < NVW; ++k) {
+          ar[k] += v[k][u].x * wv.x + v[k][u].y * wv.y;
+          ai[k] += v[k][u].x * wv.y - v[k][u].y * wv.x;
+        }
+      }
+    }
+  }
+  // per-(vector, rhs) sums over the lanes of a warp that share the rhs
+  const int nslots = nvec + 1;
+#pragma unroll
+  for (int k = 0; k < NVW; ++k) {
+    red[warp][lane] = make_double2(DOTS ? (double)ar[k] : 0.0, DOTS ? (double)ai[k] : 0.0);
+    __syncwarp();
+    const int i = warp + 8 * k;
+    if (lane < nrhs && i < nvec) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int h = 0; h < H; ++h) {
+        acc.x += red[warp][lane + h * nrhs].x;
+        acc.y += red[warp][lane + h * nrhs].y;
+      }
+      partials[((int64_t)blockIdx.x * nslots + i) * nrhs + lane] = acc;
+    }
+    __syncwarp();
+  }
+  // the norm is held by the slot threads (warps 0 .. U-1), lane l with rhs l % nrhs
+  __syncthreads();
+  red[warp][lane] = make_double2(NORM && is_slot ? (double)nn : 0.0, 0.0);
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double acc = 0.0;
+    for (int u = 0; u < U; ++u)
+      for (int h = 0; h < H; ++h) acc += red[u][threadIdx.x + h * nrhs].x;
+    partials[((int64_t)blockIdx.x * nslots + nvec) * nrhs + threadIdx.x] = make_double2(acc, 0.0);
+  }
+}
+
+template <typename C, int NVW, int U>
+static void gs_split_dispatch(int blocks, int64_t n, int nrhs, int nvec, const void* basis, int64_t vstride,
+                              void* w, const void* coef, const double* oscale, bool update, bool dots, bool norm,
+                              void* partials, const int* skip, cudaStream_t stream) {
+  const C* b = (const C*)basis;
+  C* wp = (C*)w;
+  const double2* cf = (const double2*)coef;
+  double2* pa = (double2*)partials;
+#define GSS_LAUNCH(UP, D, N) \
+  gs_split_kernel<C, NVW, U, UP, D, N><<<blocks, 256, 0, stream>>>(n, nrhs, nvec, b, vstride, wp, cf, oscale, pa, skip)
+  if (update) {
+    if (dots) { if (norm) GSS_LAUNCH(true, true, true); else GSS_LAUNCH(true, true, false); }
+    else { if (norm) GSS_LAUNCH(true, false, true); else GSS_LAUNCH(true, false, false); }
+  } else {
+    if (dots) { if (norm) GSS_LAUNCH(false, true, true); else GSS_LAUNCH(false, true, false); }
+    else GSS_LAUNCH(false, false, true);
+  }
+#undef GSS_LAUNCH
+}
+
 template <typename C, int NVB>
 static void gs_dispatch(const BlasPlan& p, int64_t n, int nvec, const void* basis, int64_t vstride,
-                        void* w, const void* coef, bool update, bool dots, bool norm, void* partials,
-                        const int* skip, cudaStream_t stream) {
+                        void* w, const void* coef, const double* oscale, bool update, bool dots, bool norm,
+                        void* partials, const int* skip, cudaStream_t stream) {
   const C* b = (const C*)basis;
   C* wp = (C*)w;
   const double2* cf = (const double2*)coef;
   double2* pa = (double2*)partials;
 #define GS_LAUNCH(U, D, N) \
-  gs_pass_kernel<C, NVB, U, D, N><<<p.blocks, p.threads, 0, stream>>>(n, p.nrhs, nvec, b, vstride, wp, cf, pa, skip)
+  gs_pass_kernel<C, NVB, U, D, N><<<p.blocks, p.threads, 0, stream>>>(n, p.nrhs, nvec, b, vstride, wp, cf, oscale, pa, skip)
   if (update) {
     if (dots) { if (norm) GS_LAUNCH(true, true, true); else GS_LAUNCH(true, true, false); }
     else { if (norm) GS_LAUNCH(true, false, true); else GS_LAUNCH(true, false, false); }
@@ -177,12 +347,28 @@ static void gs_dispatch(const BlasPlan& p, int64_t n, int nvec, const void* basi
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, const double* oscale) {
   if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
+  if (plan.split) {
+#define GSS_NVW(NW)                                                                                   \
+  if (f64) gs_split_dispatch<double2, NW, 2>(plan.blocks, n, plan.nrhs, nvec, basis, vstride, w, coef, \
+                                             oscale, update, dots, norm, partials, skip, stream);    \
+  else gs_split_dispatch<float2, NW, 4>(plan.blocks, n, plan.nrhs, nvec, basis, vstride, w, coef,      \
+                                        oscale, update, dots, norm, partials, skip, stream);
+    if (nvec <= 8) { GSS_NVW(1) }
+    else if (nvec <= 16) { GSS_NVW(2) }
+    else if (nvec <= 32) { GSS_NVW(4) }
+    else { GSS_NVW(8) }
+#undef GSS_NVW
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (!dots && !norm) return cudaSuccess;
+    return launch_reduce(plan.blocks, (nvec + 1) * plan.nrhs, partials, out, skip, stream);
+  }
 #define GS_NVB(NV)                                                                                \
-  if (f64) gs_dispatch<double2, NV>(plan, n, nvec, basis, vstride, w, coef, update, dots, norm,   \
-                                    partials, skip, stream);                                      \
-  else gs_dispatch<float2, NV>(plan, n, nvec, basis, vstride, w, coef, update, dots, norm,        \
+  if (f64) gs_dispatch<double2, NV>(plan, n, nvec, basis, vstride, w, coef, oscale, update, dots, norm, \
+                                    partials, skip, stream);                                            \
+  else gs_dispatch<float2, NV>(plan, n, nvec, basis, vstride, w, coef, oscale, update, dots, norm,        \
                                partials, skip, stream);
   if (nvec <= 4) { GS_NVB(4) }
   else if (nvec <= 8) { GS_NVB(8) }
@@ -192,6 +378,7 @@ cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, 
 #undef GS_NVB
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (!dots && !norm) return cudaSuccess;
   return launch_reduce(plan.blocks, (nvec + 1) * plan.nrhs, partials, out, skip, stream);
 }
 

@@ -2,8 +2,11 @@
 // odd-even prepare/reconstruct and the Gram-Schmidt step. The solver is in solver.cu.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "ctx.h"
@@ -107,10 +110,8 @@ static DslashArgs<Real> base_args(lqcd_ctx ctx, int nrhs, bool f64) {
 }
 
 template <typename Real>
-static cudaError_t run(const DslashArgs<Real>& a, int self_mode, int post_mode, int nrhs,
-                       cudaStream_t s) {
-  const int nr = (sizeof(Real) == 4 && nrhs % 2 == 0) ? 2 : 1;
-  return launch_dslash<Real>(a, self_mode, post_mode, nr, s);
+static cudaError_t run(const DslashArgs<Real>& a, int self_mode, int post_mode, int variant, cudaStream_t s) {
+  return launch_dslash<Real>(a, self_mode, post_mode, variant, s);
 }
 
 template <typename Real>
@@ -124,6 +125,7 @@ static lqcd_status apply_t(lqcd_ctx ctx, int op, int nrhs, const void* in, void*
   DslashArgs<Real> a = base_args<Real>(ctx, nrhs, f64);
   a.skip = skip;
   a.hop = 1;
+  const int variant = tuned_variant(ctx, f64, nrhs, op);
   if (op == LQCD_OP_FULL) {
     a.full = 1;
     a.n_target = ctx->g.V;
@@ -132,7 +134,7 @@ static lqcd_status apply_t(lqcd_ctx ctx, int op, int nrhs, const void* in, void*
     a.hop_in = (const C*)in;
     a.c_hop = (Real)-0.5;
     a.self_scalar = diag;
-    LQCD_CUDA(run<Real>(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, nrhs, stream), "dslash full");
+    LQCD_CUDA(run<Real>(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, variant, stream), "dslash full");
     return LQCD_OK;
   }
   // Schur: pass A on even sites, t_e = A_ee^{-1} D_eo psi_o
@@ -143,7 +145,7 @@ static lqcd_status apply_t(lqcd_ctx ctx, int op, int nrhs, const void* in, void*
   a.hop_in = (const C*)in;
   a.c_hop = (Real)-0.5;
   a.post_scalar = diag_inv;
-  LQCD_CUDA(run<Real>(a, SELF_NONE, clover ? POST_BLOCKINV : POST_SCALAR, nrhs, stream), "dslash schur A");
+  LQCD_CUDA(run<Real>(a, SELF_NONE, clover ? POST_BLOCKINV : POST_SCALAR, variant, stream), "dslash schur A");
   // pass B on odd sites, out = A_oo psi_o - D_oe t_e
   a.target_parity = 1;
   a.out = (C*)out;
@@ -151,7 +153,7 @@ static lqcd_status apply_t(lqcd_ctx ctx, int op, int nrhs, const void* in, void*
   a.self_in = (const C*)in;
   a.self_scalar = diag;
   a.c_hop = (Real)0.5;
-  LQCD_CUDA(run<Real>(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, nrhs, stream), "dslash schur B");
+  LQCD_CUDA(run<Real>(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, variant, stream), "dslash schur B");
   return LQCD_OK;
 }
 
@@ -177,7 +179,7 @@ static lqcd_status prepare_t(lqcd_ctx ctx, int nrhs, const void* b_full, void* b
   a.self_in = b;
   a.self_scalar = (Real)1;
   a.post_scalar = (Real)(1.0 / (4.0 + ctx->m0));
-  LQCD_CUDA(run<Real>(a, SELF_SCALAR, clover ? POST_BLOCKINV : POST_SCALAR, nrhs, stream), "prepare A_ee^-1");
+  LQCD_CUDA(run<Real>(a, SELF_SCALAR, clover ? POST_BLOCKINV : POST_SCALAR, -1, stream), "prepare A_ee^-1");
   // hat b_o = b_o - D_oe u_e = b_o + (1/2) H u_e
   a.target_parity = 1;
   a.hop = 1;
@@ -185,7 +187,7 @@ static lqcd_status prepare_t(lqcd_ctx ctx, int nrhs, const void* b_full, void* b
   a.self_in = b + a.half_elems;
   a.hop_in = (const C*)tmp_even;
   a.c_hop = (Real)0.5;
-  LQCD_CUDA(run<Real>(a, SELF_SCALAR, POST_NONE, nrhs, stream), "prepare hop");
+  LQCD_CUDA(run<Real>(a, SELF_SCALAR, POST_NONE, -1, stream), "prepare hop");
   return LQCD_OK;
 }
 
@@ -206,7 +208,7 @@ static lqcd_status reconstruct_t(lqcd_ctx ctx, int nrhs, const void* b_full, con
   a.hop_in = (const C*)x_o;
   a.c_hop = (Real)0.5;
   a.post_scalar = (Real)(1.0 / (4.0 + ctx->m0));
-  LQCD_CUDA(run<Real>(a, SELF_SCALAR, clover ? POST_BLOCKINV : POST_SCALAR, nrhs, stream), "reconstruct");
+  LQCD_CUDA(run<Real>(a, SELF_SCALAR, clover ? POST_BLOCKINV : POST_SCALAR, -1, stream), "reconstruct");
   C* xo_dst = (C*)x_full + a.half_elems;
   if ((const void*)xo_dst != x_o)
     LQCD_CUDA(cudaMemcpyAsync(xo_dst, x_o, sizeof(C) * a.half_elems, cudaMemcpyDeviceToDevice, stream),
@@ -471,6 +473,89 @@ lqcd_status lqcd_schur_reconstruct(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, con
   if (!valid_dtype(dtype) || nrhs < 1 || nrhs > 256 || !b || !x_o || !x)
     return set_error(LQCD_ERR_ARG, "lqcd_schur_reconstruct: bad arguments");
   return schur_reconstruct(ctx, dtype == LQCD_C128, nrhs, b, x_o, x, (cudaStream_t)stream);
+}
+
+
+lqcd_status lqcd_set_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op, int variant) {
+  CHECK_CTX(ctx);
+  const bool f64 = dtype == LQCD_C128;
+  if (!valid_dtype(dtype) || nrhs < 1 || nrhs > 256 || (op != LQCD_OP_FULL && op != LQCD_OP_SCHUR) ||
+      (variant != -1 && !dslash_variant_ok(f64, variant, nrhs)))
+    return set_error(LQCD_ERR_ARG, "lqcd_set_kernel_variant: bad arguments or variant %d does not fit nrhs %d",
+                     variant, nrhs);
+  if (variant == -1) ctx->tuned.erase(tune_key(f64, nrhs, op));
+  else ctx->tuned[tune_key(f64, nrhs, op)] = variant;
+  return LQCD_OK;
+}
+
+int lqcd_get_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op) {
+  if (!ctx || !valid_dtype(dtype) || nrhs < 1) return -2;
+  const bool f64 = dtype == LQCD_C128;
+  const int v = tuned_variant(ctx, f64, nrhs, op);
+  return v >= 0 ? v : dslash_default_variant(f64, nrhs);
+}
+
+int lqcd_kernel_variant_count(lqcd_dtype dtype) {
+  if (!valid_dtype(dtype)) return 0;
+  return dslash_variant_count(dtype == LQCD_C128);
+}
+
+lqcd_status lqcd_tune(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, int reps, double* times_ms, int* n_variants,
+                      void* stream) {
+  CHECK_CTX(ctx);
+  lqcd_status st = check_ready(ctx, "lqcd_tune");
+  if (st != LQCD_OK) return st;
+  if (!valid_dtype(dtype) || nrhs < 1 || nrhs > 256 || reps < 1)
+    return set_error(LQCD_ERR_ARG, "lqcd_tune: bad arguments");
+  const bool f64 = dtype == LQCD_C128;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nv = dslash_variant_count(f64);
+  if (n_variants) *n_variants = nv;
+  const size_t full_b = lqcd_packed_bytes(ctx, dtype, LQCD_SITES_FULL, nrhs);
+  void *in, *out, *tmp;
+  if ((st = workspace(ctx, "tune_in", full_b, &in)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "tune_out", full_b, &out)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "tune_tmp", full_b / 2, &tmp)) != LQCD_OK) return st;
+  LQCD_CUDA(cudaMemsetAsync(in, 0x3c, full_b, s), "tune fill");
+  cudaEvent_t e0, e1;
+  LQCD_CUDA(cudaEventCreate(&e0), "event");
+  LQCD_CUDA(cudaEventCreate(&e1), "event");
+  const int ops[2] = {LQCD_OP_FULL, LQCD_OP_SCHUR};
+  for (int oi = 0; oi < 2; ++oi) {
+    const int op = ops[oi];
+    double best = 1e300;
+    int best_v = -1;
+    ctx->tuned.erase(tune_key(f64, nrhs, op));
+    for (int v = 0; v < nv; ++v) {
+      double med = NAN;
+      if (dslash_variant_ok(f64, v, nrhs)) {
+        ctx->tuned[tune_key(f64, nrhs, op)] = v;
+        std::vector<float> t(reps);
+        for (int w = 0; w < 2; ++w)
+          if ((st = apply_operator(ctx, op, f64, nrhs, in, out, tmp, nullptr, s)) != LQCD_OK) break;
+        for (int k = 0; k < reps && st == LQCD_OK; ++k) {
+          cudaEventRecord(e0, s);
+          st = apply_operator(ctx, op, f64, nrhs, in, out, tmp, nullptr, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t[k], e0, e1);
+        }
+        if (st != LQCD_OK) break;
+        std::sort(t.begin(), t.end());
+        med = t[reps / 2];
+        if (med < best) { best = med; best_v = v; }
+      }
+      if (times_ms) times_ms[2 * v + oi] = med;
+    }
+    if (st != LQCD_OK) {
+      ctx->tuned.erase(tune_key(f64, nrhs, op));
+      break;
+    }
+    ctx->tuned[tune_key(f64, nrhs, op)] = best_v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 }  // extern "C"

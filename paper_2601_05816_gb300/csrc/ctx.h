@@ -45,6 +45,7 @@ struct lqcd_ctx_s {
   cudaStream_t capture_stream = nullptr;
   lqcd::CycleGraph cycle;
   std::vector<cudaEvent_t> prof_events;  // solver profiling events (4 per Arnoldi step)
+  std::map<long long, int> tuned;        // (f64, nrhs, op) -> hopping-kernel variant chosen by lqcd_tune
   void* pinned = nullptr;   // small pinned host staging area
   size_t pinned_bytes = 0;
 };
@@ -76,6 +77,12 @@ lqcd_status schur_prepare(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, 
                           void* tmp_even, cudaStream_t stream);
 lqcd_status schur_reconstruct(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, const void* x_o,
                               void* x_full, cudaStream_t stream);
+
+inline long long tune_key(bool f64, int nrhs, int op) { return ((long long)f64 << 40) | ((long long)nrhs << 8) | op; }
+inline int tuned_variant(const lqcd_ctx_s* ctx, bool f64, int nrhs, int op) {
+  auto it = ctx->tuned.find(tune_key(f64, nrhs, op));
+  return it == ctx->tuned.end() ? -1 : it->second;
+}
 
 inline size_t packed_elems(const lqcd_ctx_s* ctx, int sites, int nrhs) {
   const size_t ns = sites == LQCD_SITES_FULL ? (size_t)ctx->g.V : (size_t)ctx->g.Vh;

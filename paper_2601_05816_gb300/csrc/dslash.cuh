@@ -121,28 +121,14 @@ template <> struct SpinTab<3> { enum { ps0 = 1, pc0 = 3, ps1 = 0, pc1 = 3, rs0 =
 
 __host__ __device__ constexpr int neg_code(int c) { return c == 0 ? 1 : c == 1 ? 0 : c == 2 ? 3 : 2; }
 
-// One hopping direction (forward for DIR = +1, backward for DIR = -1).
+// Spin projection, SU(3) multiply and reconstruction of one hopping direction
+// (forward for DIR = +1, backward for DIR = -1) from the neighbour spinor (upper
+// spins up[6], lower spins dn[6]) and the link u[9] (row-major).
 template <typename Real, int NR, int MU, int DIR>
-__device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
-                                        const typename Cplx<Real>::T* hin, MC<Real, NR> acc[12]) {
+__device__ __forceinline__ void hop_compute(const typename Cplx<Real>::T* u, const MC<Real, NR>* up,
+                                            const MC<Real, NR>* dn, MC<Real, NR> acc[12]) {
   using C = typename Cplx<Real>::T;
   using Tab = SpinTab<MU>;
-  const int nlex = neighbour_lex<MU, DIR>(a.g, c);
-  const int ncb = nlex >> 1;
-  // link: U_mu(x) forward, U_mu(x - mu) backward (eo index of its base site)
-  const int link_site = (DIR > 0) ? (p * a.g.Vh + (c.lex >> 1)) : ((1 - p) * a.g.Vh + ncb);
-  const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
-  C u[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
-
-  // neighbour spinor: upper spins (comps 0..5), lower spins (comps 6..11)
-  MC<Real, NR> up[6], dn[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    mc_load(up[k], hin + a.lay.index(ncb, k, r0));
-    mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
-  }
   constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);
   constexpr int pc1 = DIR > 0 ? Tab::pc1 : neg_code(Tab::pc1);
   constexpr int rc0 = DIR > 0 ? Tab::rc0 : neg_code(Tab::rc0);
@@ -184,6 +170,28 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
     mc_acc<rc0>(acc[6 + col], w[3 * Tab::rs0 + col]);
     mc_acc<rc1>(acc[9 + col], w[3 * Tab::rs1 + col]);
   }
+}
+
+// One hopping direction with direct (register) loads of the link and the neighbour.
+template <typename Real, int NR, int MU, int DIR>
+__device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
+                                        const typename Cplx<Real>::T* hin, MC<Real, NR> acc[12]) {
+  using C = typename Cplx<Real>::T;
+  const int nlex = neighbour_lex<MU, DIR>(a.g, c);
+  const int ncb = nlex >> 1;
+  // link: U_mu(x) forward, U_mu(x - mu) backward (eo index of its base site)
+  const int link_site = (DIR > 0) ? (p * a.g.Vh + (c.lex >> 1)) : ((1 - p) * a.g.Vh + ncb);
+  const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
+  C u[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
+  MC<Real, NR> up[6], dn[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    mc_load(up[k], hin + a.lay.index(ncb, k, r0));
+    mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+  }
+  hop_compute<Real, NR, MU, DIR>(u, up, dn, acc);
 }
 
 // Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 strictly
@@ -248,8 +256,8 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
   block_matvec<Real, NR>(m, x + 6, y + 6);
 }
 
-template <typename Real, int NR, int SELF, int POST>
-__global__ void __launch_bounds__(256) dslash_kernel(DslashArgs<Real> a) {
+template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   using C = typename Cplx<Real>::T;
   if (a.skip != nullptr && *a.skip != 0) return;
   const int site = blockIdx.x * blockDim.y + threadIdx.y;
@@ -328,9 +336,44 @@ __global__ void __launch_bounds__(256) dslash_kernel(DslashArgs<Real> a) {
   }
 }
 
-// Host-side launcher, instantiated in dslash_f32.cu / dslash_f64.cu.
+// Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
+// nrhs/NR threads wide and threads/(nrhs/NR) sites tall) and a minimum number of
+// resident CTAs per SM (which caps the registers per thread). The autotuner
+// (lqcd_tune) times them; variant -1 is the built-in default.
+struct DslashVariant {
+  int nr, threads, minb;
+  int stages;  // 0: direct register loads; >= 2: cp.async pipeline depth (dslash_async.cuh)
+};
+int dslash_variant_count(bool f64);
+DslashVariant dslash_variant(bool f64, int idx);
+int dslash_default_variant(bool f64, int nrhs);
+bool dslash_variant_ok(bool f64, int idx, int nrhs);
+
 template <typename Real>
-cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mode, int nr,
+cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mode, int variant,
                           cudaStream_t stream);
+
+// Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
+template <typename Real, int NR, int MAXT, int MINB>
+cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
+  const int G = a.lay.nrhs / NR;
+  dim3 block(G, G >= MAXT ? 1 : MAXT / G);
+  dim3 grid((a.n_target + block.y - 1) / block.y);
+#define LQCD_DS(SM, PM) dslash_kernel<Real, NR, SM, PM, MAXT, MINB><<<grid, block, 0, s>>>(a)
+  if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
+  else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
+  else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
+  else if (self_mode == SELF_NONE && post_mode == POST_BLOCKINV) LQCD_DS(SELF_NONE, POST_BLOCKINV);
+  else if (self_mode == SELF_SCALAR && post_mode == POST_SCALAR) LQCD_DS(SELF_SCALAR, POST_SCALAR);
+  else if (self_mode == SELF_SCALAR && post_mode == POST_BLOCKINV) LQCD_DS(SELF_SCALAR, POST_BLOCKINV);
+  else return cudaErrorInvalidValue;
+#undef LQCD_DS
+  return cudaGetLastError();
+}
+
+// Explicit instantiation of one variant's launcher in its own translation unit
+// (the variants compile in parallel).
+#define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB) \
+  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB>(const DslashArgs<REAL>&, int, int, cudaStream_t);
 
 }  // namespace lqcd

@@ -1,0 +1,6 @@
+// FP64 hopping-kernel variant 0: 1 rhs per thread, 128 threads per CTA, >= 1 CTA(s) per SM.
+#include "dslash.cuh"
+
+namespace lqcd {
+LQCD_DSLASH_VARIANT_TU(double, 1, 128, 1)
+}  // namespace lqcd

@@ -27,6 +27,7 @@ struct BlasPlan {
   int nrhs;
   int threads;   // multiple of nrhs, <= 256
   int blocks;    // CTAs of the streaming kernels
+  int split;     // 1: Gram-Schmidt passes use the warp-split kernel (nrhs <= 32)
 };
 BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
 
@@ -36,10 +37,12 @@ BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
 //   if norm:   out[nvec][r] = ||w||^2 (real part)
 // out: device double2 [nvec + 1][nrhs]; partials: device scratch double2
 // [plan.blocks][nvec + 1][nrhs]. skip: optional device flag (return when set).
+//   oscale: optional device double [nrhs]; the updated w is multiplied by it before the store
+//   (dots and norm refer to the unscaled w). With neither dots nor norm no reduction runs.
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const double* oscale = nullptr);
 
 // r = b - t (all FP64) with out[0][r] = ||r||^2.
 cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
@@ -79,8 +82,10 @@ struct GmresState {
 // init: gamma = (beta0, 0, ...), done = !active, scale = active / beta0.
 cudaError_t launch_cycle_init(const GmresState& s, const double* beta0, cudaStream_t stream);
 // step j: column from h1 (+ h2 when h2 != null) and ||w||^2 = hn[j + 1][r], rotations, gamma, stop test.
+// With pythag, ||w||^2 = hn[j + 1][r] - sum_i |h2[i][r]|^2 (hn holds ||w'||^2 before the second
+// Gram-Schmidt correction h2, which is orthogonal to the final w).
 cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void* h2, const void* hn,
-                          cudaStream_t stream);
+                          bool pythag, cudaStream_t stream);
 cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream);
 
 // dslash_f32.cu / dslash_f64.cu: see dslash.cuh.

@@ -53,25 +53,26 @@ __global__ void cycle_init_kernel(GmresState s, const double* __restrict__ beta0
 // stored rotations applied to it, a new rotation (c = |a|/rho, s = (a/|a|) h/rho),
 // gamma_{j+1} = -conj(s) gamma_j, gamma_j = c gamma_j, and the stop test.
 __global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h1,
-                              const double2* __restrict__ h2, const double2* __restrict__ hn) {
+                              const double2* __restrict__ h2, const double2* __restrict__ hn, int pythag) {
   const int r = threadIdx.x;
   const int nrhs = s.nrhs;
   bool live = false;
   if (r < nrhs) {
     if (!s.done[r]) {
       double2* col = s.H + ((int64_t)r * s.m + j) * (s.m + 1);
-      double w2 = 0.0;
+      double w2 = 0.0, h2sq = 0.0;
       for (int i = 0; i <= j; ++i) {
         double2 v = h1[(int64_t)i * nrhs + r];
         if (h2 != nullptr) {
           const double2 u = h2[(int64_t)i * nrhs + r];
+          h2sq += u.x * u.x + u.y * u.y;
           v.x += u.x;
           v.y += u.y;
         }
         col[i] = v;
         w2 += v.x * v.x + v.y * v.y;
       }
-      const double beta2 = fmax(hn[(int64_t)(j + 1) * nrhs + r].x, 0.0);
+      const double beta2 = fmax(hn[(int64_t)(j + 1) * nrhs + r].x - (pythag ? h2sq : 0.0), 0.0);
       const double beta = sqrt(beta2);
       w2 += beta2;
       double* cs = s.cs + (int64_t)r * s.m;
@@ -116,7 +117,7 @@ __global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h
         s.scale[r] = 0.0;
         if (bad) s.k[r] = j;  // discard the step that produced a non-finite value
       } else {
-        s.scale[r] = 1.0 / beta;
+        s.scale[r] = beta > 0.0 ? 1.0 / beta : 0.0;
         live = true;
       }
     } else {
@@ -174,9 +175,9 @@ cudaError_t launch_cycle_init(const GmresState& s, const double* beta0, cudaStre
   return cudaGetLastError();
 }
 cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void* h2, const void* hn,
-                          cudaStream_t stream) {
+                          bool pythag, cudaStream_t stream) {
   givens_kernel<<<1, round_threads(s.nrhs), 0, stream>>>(s, j, (const double2*)h1, (const double2*)h2,
-                                                         (const double2*)hn);
+                                                         (const double2*)hn, pythag ? 1 : 0);
   return cudaGetLastError();
 }
 cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream) {
@@ -202,8 +203,14 @@ struct SolveBufs {
   BlasPlan plan;
 };
 
-// Gram-Schmidt of basis[j+1] against basis[0..j] (CGS2 or CGS1), then the Givens step.
-static lqcd_status arnoldi_ortho(lqcd_ctx ctx, const SolveBufs& b, int j, bool reorth, cudaStream_t s) {
+// Gram-Schmidt of w = basis[j+1] against basis[0..j], the Givens step, and the
+// normalisation v_{j+1} = w / beta (0 for rhs whose cycle has finished).
+//   CGS2: h1 = V^H w; w' = w - V h1 with h2 = V^H w' and ||w'||^2; Givens with
+//         beta^2 = ||w'||^2 - |h2|^2 (Pythagoras: V h2 is orthogonal to the final w);
+//         v_{j+1} = (w' - V h2) / beta in the same pass.
+//   CGS1: h1 = V^H w; w' = w - V h1 with ||w'||^2; Givens; v_{j+1} = w' / beta.
+// The profiled Gram-Schmidt time covers all of it (the one-CTA Givens kernel included).
+static lqcd_status arnoldi_ortho(const SolveBufs& b, int j, bool reorth, cudaEvent_t ev_gs_end, cudaStream_t s) {
   const int nvec = j + 1;
   char* base = (char*)b.basis;
   void* w = base + (size_t)(j + 1) * b.inner_bytes;
@@ -214,17 +221,20 @@ static lqcd_status arnoldi_ortho(lqcd_ctx ctx, const SolveBufs& b, int j, bool r
             "gs dots");
   if (reorth) {
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, true,
-                             false, b.partials, b.h2, skip, s),
-              "gs update+dots");
+                             true, b.partials, b.h2, skip, s),
+              "gs update+dots+norm");
+    LQCD_CUDA(launch_givens(b.st, j, b.h1, b.h2, b.h2, true, s), "givens");
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h2, true, false,
-                             true, b.partials, b.hn, skip, s),
-              "gs update+norm");
+                             false, b.partials, nullptr, skip, s, b.st.scale),
+              "gs update+scale");
   } else {
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, false,
                              true, b.partials, b.hn, skip, s),
               "gs update+norm");
+    LQCD_CUDA(launch_givens(b.st, j, b.h1, nullptr, b.hn, false, s), "givens");
+    LQCD_CUDA(launch_scale_inplace(b.f64_inner, b.n_sys, b.nrhs, w, b.st.scale, skip, s), "scale");
   }
-  (void)ctx;
+  if (ev_gs_end) LQCD_CUDA(cudaEventRecord(ev_gs_end, s), "event");
   return LQCD_OK;
 }
 
@@ -250,11 +260,13 @@ static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int 
 }
 
 // Algorithmic bytes of the Gram-Schmidt step with nvec basis vectors on n complex
-// elements: dots read nvec + 1 vectors; each update pass reads nvec + 1 and writes 1.
+// elements: the dot pass reads nvec + 1 vectors; each update pass reads nvec + 1
+// and writes 1 (CGS2: two updates, the second one normalising; CGS1: one update
+// and a separate normalisation that reads and writes w once more).
 static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, bool reorth) {
   const double v = (double)n * (f64 ? 16.0 : 8.0);
   const double dots = (nvec + 1) * v, upd = (nvec + 2) * v;
-  return reorth ? dots + 2 * upd : dots + upd;
+  return reorth ? dots + 2 * upd : dots + upd + 2 * v;
 }
 
 static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bool reorth, Profile* prof,
@@ -270,11 +282,8 @@ static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bo
       LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 1], s), "event");
       LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 2], s), "event");
     }
-    st = arnoldi_ortho(ctx, b, j, reorth, s);
+    st = arnoldi_ortho(b, j, reorth, prof->on ? prof->ev[4 * j + 3] : nullptr, s);
     if (st != LQCD_OK) return st;
-    if (prof->on) LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 3], s), "event");
-    LQCD_CUDA(launch_givens(b.st, j, b.h1, reorth ? b.h2 : nullptr, b.hn, s), "givens");
-    LQCD_CUDA(launch_scale_inplace(b.f64_inner, b.n_sys, b.nrhs, w, b.st.scale, b.st.all_done, s), "scale");
   }
   if (prof->on) prof->used = b.m;
   return LQCD_OK;
@@ -576,8 +585,9 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     LQCD_CUDA(launch_backsub(B.st, s), "backsub");
     LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, s),
               "update x");
-    // cycle_init, v0, per step (operator + Gram-Schmidt kernels and reductions + givens + scale), backsub, update
-    nl += 4 + (long long)m * ((eo ? 2 : 1) + (reorth ? 6 : 4) + 2);
+    // cycle_init, v0, per step (operator, Gram-Schmidt passes with their reductions, givens,
+    // normalisation), backsub, update
+    nl += 4 + (long long)m * ((eo ? 2 : 1) + 6);
     LQCD_CUDA(cudaMemcpyAsync(hs->kcycle, B.st.k, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s), "read k");
     pending_k = true;
     ++restarts;

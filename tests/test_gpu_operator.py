@@ -173,7 +173,8 @@ def test_schur_prepare_reconstruct(case, dtype):
 
 
 @pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
-@pytest.mark.parametrize("nvec,nrhs,reorth", [(1, 1, True), (5, 3, True), (17, 12, False), (32, 16, True)])
+@pytest.mark.parametrize("nvec,nrhs,reorth", [(1, 1, True), (5, 3, True), (17, 12, False), (32, 16, True),
+                                               (40, 16, True), (9, 40, True)])
 def test_orthogonalise_matches_projection(dtype, nvec, nrhs, reorth):
     """h = V^H w and w' = (1 - V V^H) w per rhs for an orthonormal basis (numpy QR)."""
     lat, *_ = setup((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0, 101)
@@ -238,3 +239,49 @@ def test_operator_sweep_lattice_sampled_rhs(dtype):
         got = out.cpu().numpy()[sample]
         assert relerr(got, ref) < TOL[dtype]
     lat.close()
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+def test_every_kernel_variant_and_tuner(dtype):
+    """Every launch variant of the hopping kernel gives the oracle's answer, and
+    the autotuner leaves a valid choice that persists through a JSON cache."""
+    dims, kind, eps, m0, c_sw = CASES[0]
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    lib = lq.load()
+    for nrhs in (4, 6):
+        psi = syn.gaussian_spinors(dims, nrhs, 500 + nrhs)
+        psi_o = oracle.split_parity(psi, 1)
+        ref_f = oracle.apply_D(U, psi, m0, C)
+        ref_s = oracle.apply_schur(U, A, Ainv, psi_o)
+        for v in range(lib.lqcd_kernel_variant_count(dtype)):
+            for op, src, ref in ((lq.OP_FULL, psi, ref_f), (lq.OP_SCHUR, psi_o, ref_s)):
+                try:
+                    lat.set_kernel_variant(dtype, nrhs, op, v)
+                except lq.LqcdError:
+                    continue      # variant does not fit nrhs
+                d_in = dev(src, dtype)
+                d_out = torch.empty_like(d_in)
+                lat.apply(op, nrhs, d_in, d_out)
+                torch.cuda.synchronize()
+                assert relerr(d_out.cpu().numpy(), ref) < TOL[dtype], (v, op, nrhs)
+        times = lat.tune(dtype, nrhs, reps=3)
+        for op in (lq.OP_FULL, lq.OP_SCHUR):
+            chosen = lat.kernel_variant(dtype, nrhs, op)
+            col = 0 if op == lq.OP_FULL else 1
+            ok = [t[col] for t in times if t[col] == t[col]]
+            assert times[chosen][col] == min(ok)
+        d_in = dev(psi_o, dtype)
+        d_out = torch.empty_like(d_in)
+        lat.apply(lq.OP_SCHUR, nrhs, d_in, d_out)
+        torch.cuda.synchronize()
+        assert relerr(d_out.cpu().numpy(), ref_s) < TOL[dtype]
+    import json, os, tempfile
+    path = os.path.join(tempfile.mkdtemp(), "tune.json")
+    keys = [(dtype, 4, lq.OP_SCHUR), (dtype, 6, lq.OP_FULL)]
+    lat.save_tuning(path, keys)
+    saved = json.load(open(path))["variants"]
+    for (d, n, o) in keys:
+        lat.set_kernel_variant(d, n, o, -1)
+    assert lat.load_tuning(path)
+    for (d, n, o) in keys:
+        assert lat.kernel_variant(d, n, o) == saved[f"{d},{n},{o}"]
