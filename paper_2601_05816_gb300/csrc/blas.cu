@@ -23,7 +23,7 @@ BlasPlan blas_plan(int64_t n, int nrhs, int num_sms) {
   // the warp-split Gram-Schmidt kernel needs nrhs <= 32 (one rhs per lane)
   p.split = nrhs <= 32 ? 1 : 0;
   if (p.split) {
-    const int64_t rows_per_tile = (32 / nrhs) * 4;
+    const int64_t rows_per_tile = (32 / nrhs) * 2;
     const int64_t tiles = (n / nrhs + rows_per_tile - 1) / rows_per_tile;
     const int64_t scap = 4 * (int64_t)num_sms;
     p.blocks = (int)(tiles < scap ? (tiles < 1 ? 1 : tiles) : scap);
@@ -211,17 +211,13 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int6
     }
   }
   Real nn = 0;
-  int parity = 0;
-  for (int64_t t = blockIdx.x; t * tile_rows < Q; t += gridDim.x, parity ^= 1) {
+  // Tile loads: each lane's NVW * U basis elements and, for slot threads, the w element.
+  // The loads of the next tile are issued before the current tile is processed
+  // (register double buffering), so they overlap its barriers and arithmetic.
+  C v[NVW][U], vn[NVW][U];
+  C w_old = C{0, 0}, wn = C{0, 0};
+  auto load_tile = [&](int64_t t, C (&vv)[NVW][U], C& ww) {
     const int64_t row0 = t * tile_rows;
-    // slot thread: its element of w
-    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
-    const bool s_ok = s_on && s_row < Q;
-    const int64_t s_e = s_row * nrhs + (s_l % nrhs);
-    C w_old = C{0, 0};
-    if (s_ok) w_old = w[s_e];
-    // warp: its basis vectors on the tile
-    C v[NVW][U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t row = row0 + hrow + (int64_t)H * u;
@@ -230,9 +226,26 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int6
 #pragma unroll
       for (int k = 0; k < NVW; ++k) {
         const int i = warp + 8 * k;
-        v[k][u] = (i < nvec && ok) ? __ldg(basis + i * vstride + e) : C{0, 0};
+        vv[k][u] = (i < nvec && ok) ? __ldg(basis + i * vstride + e) : C{0, 0};
       }
     }
+    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
+    ww = (s_on && s_row < Q) ? w[s_row * nrhs + (s_l % nrhs)] : C{0, 0};
+  };
+  int parity = 0;
+  int64_t t = blockIdx.x;
+  if (t * tile_rows < Q) load_tile(t, vn, wn);
+  for (; t * tile_rows < Q; t += gridDim.x, parity ^= 1) {
+#pragma unroll
+    for (int k = 0; k < NVW; ++k)
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[k][u] = vn[k][u];
+    w_old = wn;
+    if ((t + gridDim.x) * tile_rows < Q) load_tile(t + gridDim.x, vn, wn);
+    const int64_t row0 = t * tile_rows;
+    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
+    const bool s_ok = s_on && s_row < Q;
+    const int64_t s_e = s_row * nrhs + (s_l % nrhs);
     if (UPDATE) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -350,11 +363,13 @@ cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, 
                            cudaStream_t stream, const double* oscale) {
   if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
   if (plan.split) {
-#define GSS_NVW(NW)                                                                                   \
-  if (f64) gs_split_dispatch<double2, NW, 2>(plan.blocks, n, plan.nrhs, nvec, basis, vstride, w, coef, \
-                                             oscale, update, dots, norm, partials, skip, stream);    \
-  else gs_split_dispatch<float2, NW, 4>(plan.blocks, n, plan.nrhs, nvec, basis, vstride, w, coef,      \
-                                        oscale, update, dots, norm, partials, skip, stream);
+#define GSS_NVW(NW)                                                                                    \
+  if (f64) gs_split_dispatch<double2, NW, (NW >= 4 ? 1 : 4 / NW)>(plan.blocks, n, plan.nrhs, nvec, basis, \
+                                             vstride, w, coef, oscale, update, dots, norm, partials,    \
+                                             skip, stream);                                             \
+  else gs_split_dispatch<float2, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, n, plan.nrhs, nvec, basis,      \
+                                        vstride, w, coef, oscale, update, dots, norm, partials, skip,   \
+                                        stream);
     if (nvec <= 8) { GSS_NVW(1) }
     else if (nvec <= 16) { GSS_NVW(2) }
     else if (nvec <= 32) { GSS_NVW(4) }

@@ -95,6 +95,37 @@ __device__ __forceinline__ void mc_load(MC<double, 1>& a, const double2* p) {
   double2 v = __ldg(p);
   a.re[0] = v.x; a.im[0] = v.y;
 }
+// Loads issued as volatile PTX: they keep their program order, so the link and
+// neighbour loads of one direction leave the SM back to back (one memory round
+// trip per direction) instead of being spread between the arithmetic.
+__device__ __forceinline__ float4 ldg_batch(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ldg_batch(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ldg_batch(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void mc_load_batch(MC<float, 2>& a, const float2* p) {
+  const float4 v = ldg_batch(reinterpret_cast<const float4*>(p));
+  a.re[0] = v.x; a.im[0] = v.y; a.re[1] = v.z; a.im[1] = v.w;
+}
+__device__ __forceinline__ void mc_load_batch(MC<float, 1>& a, const float2* p) {
+  const float2 v = ldg_batch(p);
+  a.re[0] = v.x; a.im[0] = v.y;
+}
+__device__ __forceinline__ void mc_load_batch(MC<double, 1>& a, const double2* p) {
+  const double2 v = ldg_batch(p);
+  a.re[0] = v.x; a.im[0] = v.y;
+}
+
 __device__ __forceinline__ void mc_store(float2* p, const MC<float, 2>& a) {
   *reinterpret_cast<float4*>(p) = make_float4(a.re[0], a.im[0], a.re[1], a.im[1]);
 }
@@ -172,8 +203,9 @@ __device__ __forceinline__ void hop_compute(const typename Cplx<Real>::T* u, con
   }
 }
 
-// One hopping direction with direct (register) loads of the link and the neighbour.
-template <typename Real, int NR, int MU, int DIR>
+// One hopping direction with direct (register) loads of the link and the neighbour
+// (BATCH: as one batch of volatile loads).
+template <typename Real, int NR, int MU, int DIR, bool BATCH>
 __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
                                         const typename Cplx<Real>::T* hin, MC<Real, NR> acc[12]) {
   using C = typename Cplx<Real>::T;
@@ -183,13 +215,22 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
   const int link_site = (DIR > 0) ? (p * a.g.Vh + (c.lex >> 1)) : ((1 - p) * a.g.Vh + ncb);
   const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
   C u[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
   MC<Real, NR> up[6], dn[6];
+  if (BATCH) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    mc_load(up[k], hin + a.lay.index(ncb, k, r0));
-    mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+    for (int e = 0; e < 9; ++e) u[e] = ldg_batch(lp + (int64_t)e * a.g.V);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mc_load_batch(up[k], hin + a.lay.index(ncb, k, r0));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mc_load_batch(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+  } else {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      mc_load(up[k], hin + a.lay.index(ncb, k, r0));
+      mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+    }
   }
   hop_compute<Real, NR, MU, DIR>(u, up, dn, acc);
 }
@@ -256,7 +297,7 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
   block_matvec<Real, NR>(m, x + 6, y + 6);
 }
 
-template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB>
+template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH>
 __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   using C = typename Cplx<Real>::T;
   if (a.skip != nullptr && *a.skip != 0) return;
@@ -280,14 +321,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   if (a.hop) {
     const Coord c = site_coords(a.g, p, cb);
     const C* hin = a.full ? a.hop_in + (1 - p) * a.half_elems : a.hop_in;
-    hop_dir<Real, NR, 0, +1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 0, -1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, +1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, -1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, +1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, -1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, +1>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, -1>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, +1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, -1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, +1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, -1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, +1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, -1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, +1, BATCH>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, -1, BATCH>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -343,6 +384,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
 struct DslashVariant {
   int nr, threads, minb;
   int stages;  // 0: direct register loads; >= 2: cp.async pipeline depth (dslash_async.cuh)
+  int batch;   // direct loads: 1 = each direction's loads issued as one batch
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -354,12 +396,12 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
                           cudaStream_t stream);
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
-template <typename Real, int NR, int MAXT, int MINB>
+template <typename Real, int NR, int MAXT, int MINB, bool BATCH>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
   dim3 grid((a.n_target + block.y - 1) / block.y);
-#define LQCD_DS(SM, PM) dslash_kernel<Real, NR, SM, PM, MAXT, MINB><<<grid, block, 0, s>>>(a)
+#define LQCD_DS(SM, PM) dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH><<<grid, block, 0, s>>>(a)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -373,7 +415,7 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
 
 // Explicit instantiation of one variant's launcher in its own translation unit
 // (the variants compile in parallel).
-#define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB) \
-  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+#define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB, BATCH) \
+  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, BATCH>(const DslashArgs<REAL>&, int, int, cudaStream_t);
 
 }  // namespace lqcd

@@ -1,6 +1,6 @@
-// FP32 hopping-kernel variant 9: cp.async pipeline of 4 stages, 1 rhs per thread, 128 threads per CTA.
-#include "dslash_async.cuh"
+// FP32 hopping-kernel variant 9: 2 rhs per thread, 128 threads per CTA, >= 4 CTA(s) per SM, batched loads.
+#include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_ASYNC_VARIANT_TU(float, 1, 128, 1, 4)
+LQCD_DSLASH_VARIANT_TU(float, 2, 128, 4, true)
 }  // namespace lqcd
