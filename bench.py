@@ -280,16 +280,23 @@ def run_kernel_workload(args, w):
     else:
         nvec = w["nvec"]
         n = (V // 2) * 12 * nrhs
-        basis = torch.randn(nvec * n, dtype=torch.complex64, device="cuda", generator=g)
+        bf16 = args.precision == "bf16"
+        if bf16:   # BF16 pairs in 32-bit words
+            basis = torch.randint(-2**30, 2**30, (nvec * n,), dtype=torch.int32, device="cuda", generator=g)
+            basis &= 0x3f7f3f7f   # finite BF16 values of magnitude < 1
+        else:
+            basis = torch.randn(nvec * n, dtype=torch.complex64, device="cuda", generator=g)
         wv = torch.randn(n, dtype=torch.complex64, device="cuda", generator=g)
         h = torch.empty((nvec, nrhs), dtype=torch.complex128, device="cuda")
         hn = torch.empty(nrhs, dtype=torch.float64, device="cuda")
 
         def step():
-            lat.orthogonalise(lq.SITES_ODD, nrhs, nvec, basis, wv, h, hn, reorth=True)
-        nbytes = n * 8 * ((nvec + 1) + 2 * (nvec + 2))
+            lat.orthogonalise(lq.SITES_ODD, nrhs, nvec, basis, wv, h, hn, reorth=True,
+                              dtype=lq.BF16S if bf16 else lq.C64)
+        vb = 4 if bf16 else 8
+        nbytes = 3 * nvec * n * vb + n * 8 * 5
         launches = 7
-        kernel = "gs_pass_kernel<float2> (CGS2 step: dots, update+dots, update+norm, 3 reductions)"
+        kernel = f"gs_split_kernel ({'BF16' if bf16 else 'FP32'} basis; CGS2 step: dots, update+dots, update+norm)"
     for _ in range(args.warmup):
         step()
     s = torch.cuda.current_stream()
@@ -347,8 +354,9 @@ def run_gpu(args, w):
     x_d = torch.zeros_like(b_d)
     lat = lq.Lattice(dims, time_bc=-1)
     peak, peak_kind = measured_peaks()
-    solve_kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=w["restart"], tol=w["tol"], max_restarts=500,
-                    use_graph=True, profile=True)
+    inner = {"c64": lq.C64, "bf16": lq.BF16S}[args.precision]
+    solve_kw = dict(op=lq.OP_SCHUR, precision=inner, restart_len=w["restart"], tol=w["tol"],
+                    max_restarts=args.max_restarts, use_graph=True, profile=True)
 
     # set-up: autotune the hopping kernel for the inner (FP32) and outer (FP64) operators
     lat.set_gauge(U_d)
@@ -406,10 +414,15 @@ def run_gpu(args, w):
 
     line = {"metric": METRIC, "value": value, "unit": "site·rhs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "fp32 inner / fp64 refinement", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"c64": "fp32 inner / fp64 refinement",
+                      "bf16": "fp32 arithmetic, bf16 Arnoldi basis / fp64 refinement"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": w["name"], "lattice": "x".join(str(d) for d in dims[::-1]), "nrhs": nrhs,
                        "gauge": f"exp(i*{w['eps']}*H)", "m0": w["m0"], "c_sw": w["c_sw"],
+                       "m0_prescribed": w.get("m0_prescribed", w["m0"]),
                        "solver": f"odd-even GMRES({w['restart']}) FP32 inside FP64 restarts, tol {w['tol']}",
+                       "basis_storage": args.precision,
                        "parallelism": f"rhs batches, {world} independent rank(s)",
                        "l2": "working set (basis 33 x %.0f MB) far above the 129 MB L2" %
                              ((V // 2) * 12 * nrhs * 8 / 1e6)},
@@ -447,17 +460,26 @@ def run_gpu(args, w):
         x_d.zero_()
         t0 = time.perf_counter()
         r64 = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=lq.C128, restart_len=w["restart"], tol=w["tol"],
-                        max_restarts=500, use_graph=True)
+                        max_restarts=args.max_restarts, use_graph=True)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         mixed_s = statistics.mean(r.seconds for r in results)
         x_d.zero_()
         rg = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, profile=False))
         torch.cuda.synchronize()
+        other = {}
+        for name, prec in (("c64", lq.C64), ("bf16", lq.BF16S)):
+            if prec == inner:
+                continue
+            x_d.zero_()
+            ro = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, precision=prec, profile=False))
+            torch.cuda.synchronize()
+            other[name] = {"seconds": ro.seconds, "iterations": ro.iterations, "restarts": ro.restarts,
+                           "relres": ro.relres_max}
         line["gmres"] = {"fp64_s": t64, "mixed_s": mixed_s, "speedup": t64 / mixed_s,
                          "fp64_iterations": r64.iterations, "mixed_iterations": results[-1].iterations,
                          "fp64_relres": r64.relres_max, "mixed_relres": results[-1].relres_max,
-                         "mixed_graph_s": rg.seconds,
+                         "mixed_graph_s": rg.seconds, "other_inner_storage": other,
                          "note": "host wall time of one synchronised solve (step includes set_gauge/set_clover)"}
         # end to end through the C ABI with pinned host buffers
         U_h = torch.from_numpy(U).pin_memory()
@@ -510,10 +532,19 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ref-sample-iters", type=int, default=4)
     ap.add_argument("--ref-iterations", type=int, default=300)
+    ap.add_argument("--m0", type=float, default=None,
+                    help="companion run: replace the workload's bare mass (reported as such in config)")
+    ap.add_argument("--max-restarts", type=int, default=500)
+    ap.add_argument("--precision", default="c64", choices=["c64", "bf16"],
+                    help="inner Arnoldi basis storage of the timed solve (FP32 arithmetic either way)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.m0 is not None:
+        w["m0_prescribed"] = w["m0"]
+        w["m0"] = args.m0
+        w["name"] += f" (companion run, m0 {args.m0} instead of {w['m0_prescribed']})"
     if args.impl == "reference":
         run_reference(args, w)
     elif w.get("kind") in ("apply", "ortho"):

@@ -63,7 +63,9 @@ enum {
 
 typedef enum {
   LQCD_C64 = 1,    /* complex64: FP32 storage and arithmetic */
-  LQCD_C128 = 2    /* complex128: FP64 storage and arithmetic */
+  LQCD_C128 = 2,   /* complex128: FP64 storage and arithmetic */
+  LQCD_BF16S = 3   /* BF16 storage (re, im pairs), FP32 arithmetic: packed blocks only, see
+                      lqcd_pack and lqcd_apply_packed; as solve precision, the Arnoldi basis */
 } lqcd_dtype;
 
 typedef enum {
@@ -123,7 +125,9 @@ size_t lqcd_packed_bytes(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int n
  * Sec. III-A-2's remark that reordering before and after a solve is cheap).
  * in/out: device; canonical complex[nrhs][n_sites][4][3] of `dtype`, packed as
  * described above. For sites = FULL the canonical block lists all V sites in
- * site order; for EVEN/ODD it lists that parity's V/2 sites. */
+ * site order; for EVEN/ODD it lists that parity's V/2 sites. For LQCD_BF16S the
+ * canonical side is complex64 and the packed side BF16 (rounded to nearest even
+ * when packing). */
 lqcd_status lqcd_pack(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
                       const void* in, void* out, void* stream);
 lqcd_status lqcd_unpack(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
@@ -135,12 +139,15 @@ lqcd_status lqcd_unpack(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nr
  * op = SCHUR: in/out are odd-site packed blocks (V/2 sites); the intermediate
  * A_ee^{-1} D_eo psi lives in library workspace (allocated on first use for
  * this (dtype, nrhs), then reused). in and out must not overlap.
+ * dtype LQCD_BF16S: in is a BF16 packed block, out a complex64 packed block,
+ * arithmetic (and the Schur intermediate) in FP32; nrhs <= 128.
  * nrhs: 1..256. Requires set_gauge and set_clover. */
 lqcd_status lqcd_apply_packed(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs,
                               const void* in, void* out, void* stream);
 
 /* Same operator on canonical-layout device blocks: packs, applies, unpacks
- * through library workspace. */
+ * through library workspace. For LQCD_BF16S, in and out are complex64 blocks and
+ * the input is rounded to BF16 when packed. */
 lqcd_status lqcd_apply(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs,
                        const void* in, void* out, void* stream);
 
@@ -179,6 +186,7 @@ lqcd_status lqcd_schur_reconstruct(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
  * h_norm = ||w||. basis: device, nvec packed blocks back to back (each
  * lqcd_packed_bytes(dtype, sites, nrhs) bytes); w: device packed block, updated
  * in place. h: device, complex128 [nvec][nrhs]; hnorm: device, double [nrhs].
+ * dtype LQCD_BF16S: BF16 basis, complex64 w, FP32 arithmetic (nrhs <= 32).
  * nvec: 1..129. Dot products accumulate per thread in the vector precision and
  * across threads in FP64, in a fixed order (deterministic). */
 lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
@@ -188,7 +196,8 @@ lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites,
 typedef struct {
   int op;             /* LQCD_OP_FULL: GMRES on D; LQCD_OP_SCHUR: on S, x_e reconstructed */
   int precision;      /* LQCD_C128: FP64 Arnoldi; LQCD_C64: FP32 operator and Arnoldi
-                         inside FP64 restarts (iterative refinement) */
+                         inside FP64 restarts (iterative refinement); LQCD_BF16S: as C64
+                         with the Arnoldi basis stored in BF16 (CGS2 always, nrhs <= 32) */
   int restart_len;    /* m, 1..64 */
   int max_restarts;   /* >= 1 */
   double tol;         /* stop when ||b - D x|| <= tol ||b|| (true residual, per rhs) */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblqcd.so")
 # status codes and enums (include/lqcd.h)
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_SINGULAR, ERR_STATE = -1, -2, -3, -4, -5, -6
-C64, C128 = 1, 2
+C64, C128, BF16S = 1, 2, 3
 OP_FULL, OP_SCHUR = 0, 1
 SITES_FULL, SITES_EVEN, SITES_ODD = 0, 1, 2
 
@@ -198,25 +198,32 @@ class Lattice:
         return int(self._lib.lqcd_packed_bytes(self._h, int(dtype), int(sites), int(nrhs)))
 
     def packed_empty(self, dtype: int, sites: int, nrhs: int):
+        """Device buffer for a packed block: complex128 / complex64, or int32 words holding BF16 pairs."""
         import torch
+        if dtype == BF16S:
+            return torch.empty(self.packed_bytes(dtype, sites, nrhs) // 4, dtype=torch.int32, device="cuda")
         n = self.packed_bytes(dtype, sites, nrhs) // (16 if dtype == C128 else 8)
         return torch.empty(n, dtype=torch.complex128 if dtype == C128 else torch.complex64, device="cuda")
 
-    def pack(self, sites: int, nrhs: int, src, dst, stream=None):
-        _check(self._lib.lqcd_pack(self._h, _dtype_code(src), int(sites), int(nrhs), _ptr(src), _ptr(dst),
-                                   _stream(stream)), "lqcd_pack")
+    def pack(self, sites: int, nrhs: int, src, dst, stream=None, dtype=None):
+        d = _dtype_code(src) if dtype is None else int(dtype)
+        _check(self._lib.lqcd_pack(self._h, d, int(sites), int(nrhs), _ptr(src), _ptr(dst), _stream(stream)),
+               "lqcd_pack")
 
-    def unpack(self, sites: int, nrhs: int, src, dst, stream=None):
-        _check(self._lib.lqcd_unpack(self._h, _dtype_code(src), int(sites), int(nrhs), _ptr(src), _ptr(dst),
-                                     _stream(stream)), "lqcd_unpack")
+    def unpack(self, sites: int, nrhs: int, src, dst, stream=None, dtype=None):
+        d = _dtype_code(dst) if dtype is None else int(dtype)
+        _check(self._lib.lqcd_unpack(self._h, d, int(sites), int(nrhs), _ptr(src), _ptr(dst), _stream(stream)),
+               "lqcd_unpack")
 
-    def apply_packed(self, op: int, nrhs: int, src, dst, stream=None):
-        _check(self._lib.lqcd_apply_packed(self._h, int(op), _dtype_code(src), int(nrhs), _ptr(src), _ptr(dst),
-                                           _stream(stream)), "lqcd_apply_packed")
+    def apply_packed(self, op: int, nrhs: int, src, dst, stream=None, dtype=None):
+        d = _dtype_code(src) if dtype is None else int(dtype)
+        _check(self._lib.lqcd_apply_packed(self._h, int(op), d, int(nrhs), _ptr(src), _ptr(dst), _stream(stream)),
+               "lqcd_apply_packed")
 
-    def apply(self, op: int, nrhs: int, src, dst, stream=None):
-        _check(self._lib.lqcd_apply(self._h, int(op), _dtype_code(src), int(nrhs), _ptr(src), _ptr(dst),
-                                    _stream(stream)), "lqcd_apply")
+    def apply(self, op: int, nrhs: int, src, dst, stream=None, dtype=None):
+        d = _dtype_code(src) if dtype is None else int(dtype)
+        _check(self._lib.lqcd_apply(self._h, int(op), d, int(nrhs), _ptr(src), _ptr(dst), _stream(stream)),
+               "lqcd_apply")
 
     def schur_prepare(self, nrhs: int, b_full, bhat_o, stream=None):
         _check(self._lib.lqcd_schur_prepare(self._h, _dtype_code(b_full), int(nrhs), _ptr(b_full), _ptr(bhat_o),
@@ -227,8 +234,9 @@ class Lattice:
                                                 _ptr(x_full), _stream(stream)), "lqcd_schur_reconstruct")
 
     def orthogonalise(self, sites: int, nrhs: int, nvec: int, basis, w, h, hnorm, reorth: bool = True,
-                      stream=None):
-        _check(self._lib.lqcd_orthogonalise(self._h, _dtype_code(w), int(sites), int(nrhs), int(nvec),
+                      stream=None, dtype=None):
+        d = _dtype_code(w) if dtype is None else int(dtype)
+        _check(self._lib.lqcd_orthogonalise(self._h, d, int(sites), int(nrhs), int(nvec),
                                             _ptr(basis), _ptr(w), _ptr(h), _ptr(hnorm), int(bool(reorth)),
                                             _stream(stream)), "lqcd_orthogonalise")
 

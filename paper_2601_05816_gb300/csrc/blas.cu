@@ -35,6 +35,22 @@ template <typename C> struct RealOf;
 template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<double2> { using T = double; };
 
+// Basis storage -> compute type, and back (BF16 storage computes in FP32; rounding to nearest even).
+__device__ __forceinline__ float2 to_c(float2 v) { return v; }
+__device__ __forceinline__ double2 to_c(double2 v) { return v; }
+__device__ __forceinline__ float2 to_c(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+// Read-only load of a basis element. A BF16 pair is read as one 32-bit word and
+// widened with shifts (a BF16 value is the upper half of the FP32 bit pattern).
+template <typename C>
+__device__ __forceinline__ C ld_basis(const C* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_basis(const __nv_bfloat162* p) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ void store_as(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void store_as(double2* p, double2 v) { *p = v; }
+__device__ __forceinline__ void store_as(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
 // Block reduction of per-thread values (one per slot) into partials[blockIdx][slot][rhs].
 template <int NS>
 __device__ __forceinline__ void block_reduce_slots(const double (&vr)[NS], const double (&vi)[NS],
@@ -174,11 +190,11 @@ gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64
 // updated tile goes through shared memory to every warp for the dot products.
 // Registers stay low (several CTAs per SM) and each lane keeps NVW * U vector
 // loads in flight.
-template <typename C, int NVW, int U, bool UPDATE, bool DOTS, bool NORM>
+template <typename C, typename B, int NVW, int U, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(256)
-gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64_t vstride,
+gs_split_kernel(int64_t n, int nrhs, int nvec, const B* __restrict__ basis, int64_t vstride,
                 C* __restrict__ w, const double2* __restrict__ coef, const double* __restrict__ oscale,
-                double2* __restrict__ partials, const int* skip) {
+                B* __restrict__ wout, double2* __restrict__ partials, const int* skip) {
   using Real = typename RealOf<C>::T;
   static_assert(32 * U <= 256, "one slot thread per tile element");
   if (skip != nullptr && *skip != 0) return;
@@ -226,7 +242,7 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int6
 #pragma unroll
       for (int k = 0; k < NVW; ++k) {
         const int i = warp + 8 * k;
-        vv[k][u] = (i < nvec && ok) ? __ldg(basis + i * vstride + e) : C{0, 0};
+        vv[k][u] = (i < nvec && ok) ? C(ld_basis(basis + i * vstride + e)) : C{0, 0};
       }
     }
     const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
@@ -267,7 +283,11 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int6
           si += pq.y;
         }
         const C w_new = C{w_old.x - sr, w_old.y - si};
-        if (s_ok) w[s_e] = C{w_new.x * s_scale, w_new.y * s_scale};
+        if (s_ok) {
+          const C ws = C{w_new.x * s_scale, w_new.y * s_scale};
+          if (wout != nullptr) store_as(wout + s_e, ws);  // the normalised vector goes to the basis
+          else w[s_e] = ws;
+        }
         wsm[parity][slot] = w_new;
         if (NORM) nn += w_new.x * w_new.x + w_new.y * w_new.y;
       }
@@ -317,16 +337,18 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int6
   }
 }
 
-template <typename C, int NVW, int U>
+template <typename C, typename B, int NVW, int U>
 static void gs_split_dispatch(int blocks, int64_t n, int nrhs, int nvec, const void* basis, int64_t vstride,
-                              void* w, const void* coef, const double* oscale, bool update, bool dots, bool norm,
-                              void* partials, const int* skip, cudaStream_t stream) {
-  const C* b = (const C*)basis;
+                              void* w, const void* coef, const double* oscale, void* wout, bool update, bool dots,
+                              bool norm, void* partials, const int* skip, cudaStream_t stream) {
+  const B* b = (const B*)basis;
   C* wp = (C*)w;
+  B* wo = (B*)wout;
   const double2* cf = (const double2*)coef;
   double2* pa = (double2*)partials;
-#define GSS_LAUNCH(UP, D, N) \
-  gs_split_kernel<C, NVW, U, UP, D, N><<<blocks, 256, 0, stream>>>(n, nrhs, nvec, b, vstride, wp, cf, oscale, pa, skip)
+#define GSS_LAUNCH(UP, D, N)                                                                             \
+  gs_split_kernel<C, B, NVW, U, UP, D, N><<<blocks, 256, 0, stream>>>(n, nrhs, nvec, b, vstride, wp, cf, \
+                                                                      oscale, wo, pa, skip)
   if (update) {
     if (dots) { if (norm) GSS_LAUNCH(true, true, true); else GSS_LAUNCH(true, true, false); }
     else { if (norm) GSS_LAUNCH(true, false, true); else GSS_LAUNCH(true, false, false); }
@@ -360,16 +382,17 @@ static void gs_dispatch(const BlasPlan& p, int64_t n, int nvec, const void* basi
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
-                           cudaStream_t stream, const double* oscale) {
+                           cudaStream_t stream, const double* oscale, bool basis_bf16, void* wout) {
   if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
+  if (basis_bf16 && (f64 || !plan.split)) return cudaErrorInvalidValue;
   if (plan.split) {
-#define GSS_NVW(NW)                                                                                    \
-  if (f64) gs_split_dispatch<double2, NW, (NW >= 4 ? 1 : 4 / NW)>(plan.blocks, n, plan.nrhs, nvec, basis, \
-                                             vstride, w, coef, oscale, update, dots, norm, partials,    \
-                                             skip, stream);                                             \
-  else gs_split_dispatch<float2, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, n, plan.nrhs, nvec, basis,      \
-                                        vstride, w, coef, oscale, update, dots, norm, partials, skip,   \
-                                        stream);
+#define GSS_NVW(NW)                                                                                       \
+  if (f64) gs_split_dispatch<double2, double2, NW, (NW >= 4 ? 1 : 4 / NW)>(plan.blocks, n, plan.nrhs, nvec, \
+      basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);                  \
+  else if (basis_bf16) gs_split_dispatch<float2, __nv_bfloat162, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, \
+      n, plan.nrhs, nvec, basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream); \
+  else gs_split_dispatch<float2, float2, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, n, plan.nrhs, nvec,       \
+      basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);
     if (nvec <= 8) { GSS_NVW(1) }
     else if (nvec <= 16) { GSS_NVW(2) }
     else if (nvec <= 32) { GSS_NVW(4) }
@@ -469,11 +492,26 @@ static int stream_blocks(int64_t n, int threads) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+template <>
+__global__ void scale_convert_kernel<__nv_bfloat162>(int64_t n, int nrhs, const double2* __restrict__ src,
+                                                     const double* __restrict__ scale,
+                                                     __nv_bfloat162* __restrict__ dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double s = scale[e % nrhs];
+    const double2 v = src[e];
+    dst[e] = __float22bfloat162_rn(make_float2((float)(v.x * s), (float)(v.y * s)));
+  }
+}
+
 cudaError_t launch_scale_convert(bool dst_f64, int64_t n, int nrhs, const void* src,
-                                 const double* scale, void* dst, cudaStream_t stream) {
+                                 const double* scale, void* dst, cudaStream_t stream, bool dst_bf16) {
   const int threads = 256;
   const int blocks = stream_blocks(n, threads);
-  if (dst_f64)
+  if (dst_bf16)
+    scale_convert_kernel<__nv_bfloat162><<<blocks, threads, 0, stream>>>(n, nrhs, (const double2*)src, scale,
+                                                                         (__nv_bfloat162*)dst);
+  else if (dst_f64)
     scale_convert_kernel<double2><<<blocks, threads, 0, stream>>>(n, nrhs, (const double2*)src, scale,
                                                                   (double2*)dst);
   else
@@ -510,9 +548,9 @@ cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const d
 // x += sum_i y[i][r] v_i with the sum formed in the basis precision (the
 // correction of one restart cycle; its rounding is removed by the next FP64
 // true residual) and added to x in FP64.
-template <typename C>
+template <typename C, typename B>
 __global__ void __launch_bounds__(256)
-update_x_kernel(int64_t n, int nrhs, const C* __restrict__ basis, int64_t vstride,
+update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstride,
                 const double2* __restrict__ y, const int* __restrict__ kmax, double2* __restrict__ x) {
   using Real = typename RealOf<C>::T;
   extern __shared__ double2 ys[];
@@ -526,7 +564,7 @@ update_x_kernel(int64_t n, int nrhs, const C* __restrict__ basis, int64_t vstrid
     Real sr = 0, si = 0;
     for (int i = 0; i < k; ++i) {
       const double2 c = ys[i * nrhs + r];
-      const C v = __ldg(basis + i * vstride + e);
+      const C v = C(ld_basis(basis + i * vstride + e));
       const Real crr = (Real)c.x, cii = (Real)c.y;
       sr += crr * v.x - cii * v.y;
       si += crr * v.y + cii * v.x;
@@ -540,16 +578,19 @@ update_x_kernel(int64_t n, int nrhs, const C* __restrict__ basis, int64_t vstrid
 
 cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
                             int64_t vstride, const void* y, const int* kmax, void* x,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, bool basis_bf16) {
   const int threads = nrhs * (256 / nrhs);
   const int blocks = stream_blocks(n, threads);
   const size_t smem = sizeof(double2) * (size_t)nvec_max * nrhs;
-  if (basis_f64)
-    update_x_kernel<double2><<<blocks, threads, smem, stream>>>(n, nrhs, (const double2*)basis, vstride,
-                                                                (const double2*)y, kmax, (double2*)x);
+  if (basis_bf16)
+    update_x_kernel<float2, __nv_bfloat162><<<blocks, threads, smem, stream>>>(
+        n, nrhs, (const __nv_bfloat162*)basis, vstride, (const double2*)y, kmax, (double2*)x);
+  else if (basis_f64)
+    update_x_kernel<double2, double2><<<blocks, threads, smem, stream>>>(n, nrhs, (const double2*)basis, vstride,
+                                                                         (const double2*)y, kmax, (double2*)x);
   else
-    update_x_kernel<float2><<<blocks, threads, smem, stream>>>(n, nrhs, (const float2*)basis, vstride,
-                                                               (const double2*)y, kmax, (double2*)x);
+    update_x_kernel<float2, float2><<<blocks, threads, smem, stream>>>(n, nrhs, (const float2*)basis, vstride,
+                                                                       (const double2*)y, kmax, (double2*)x);
   return cudaGetLastError();
 }
 

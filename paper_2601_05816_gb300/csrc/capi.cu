@@ -163,6 +163,43 @@ lqcd_status apply_operator(lqcd_ctx ctx, int op, bool f64, int nrhs, const void*
              : apply_t<float>(ctx, op, nrhs, in, out, tmp, skip, stream);
 }
 
+// The operator on a BF16-stored input block with FP32 arithmetic, FP32 output
+// (and FP32 Schur intermediate tmp).
+lqcd_status apply_operator_bf16in(lqcd_ctx ctx, int op, int nrhs, const void* in, void* out, void* tmp,
+                                  const int* skip, cudaStream_t stream) {
+  const bool clover = ctx->c_sw != 0.0;
+  DslashArgs<float> a = base_args<float>(ctx, nrhs, false);
+  a.skip = skip;
+  a.hop = 1;
+  if (op == LQCD_OP_FULL) {
+    a.full = 1;
+    a.n_target = ctx->g.V;
+    a.out = (float2*)out;
+    a.self_in = (const float2*)in;   // BF16 storage, reinterpreted by the kernel
+    a.hop_in = (const float2*)in;
+    a.c_hop = -0.5f;
+    a.self_scalar = (float)(4.0 + ctx->m0);
+    LQCD_CUDA(launch_dslash_bf16(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, true, stream), "dslash bf16 full");
+    return LQCD_OK;
+  }
+  a.full = 0;
+  a.n_target = ctx->g.Vh;
+  a.target_parity = 0;
+  a.out = (float2*)tmp;
+  a.hop_in = (const float2*)in;
+  a.c_hop = -0.5f;
+  a.post_scalar = (float)(1.0 / (4.0 + ctx->m0));
+  LQCD_CUDA(launch_dslash_bf16(a, SELF_NONE, clover ? POST_BLOCKINV : POST_SCALAR, true, stream), "dslash bf16 A");
+  a.target_parity = 1;
+  a.out = (float2*)out;
+  a.hop_in = (const float2*)tmp;
+  a.self_in = (const float2*)in;
+  a.self_scalar = (float)(4.0 + ctx->m0);
+  a.c_hop = 0.5f;
+  LQCD_CUDA(launch_dslash_bf16(a, clover ? SELF_BLOCK : SELF_SCALAR, POST_NONE, false, stream), "dslash bf16 B");
+  return LQCD_OK;
+}
+
 template <typename Real>
 static lqcd_status prepare_t(lqcd_ctx ctx, int nrhs, const void* b_full, void* bhat_o, void* tmp_even,
                              cudaStream_t stream) {
@@ -244,6 +281,8 @@ static lqcd_status check_ready(lqcd_ctx ctx, const char* fn) {
 }
 
 static bool valid_dtype(int d) { return d == LQCD_C64 || d == LQCD_C128; }
+static bool valid_storage(int d) { return d == LQCD_C64 || d == LQCD_C128 || d == LQCD_BF16S; }
+static size_t elem_bytes(int d) { return d == LQCD_C128 ? 16 : (d == LQCD_C64 ? 8 : 4); }
 static bool valid_sites(int s) { return s == LQCD_SITES_FULL || s == LQCD_SITES_EVEN || s == LQCD_SITES_ODD; }
 
 extern "C" {
@@ -386,18 +425,18 @@ int lqcd_site_tile(lqcd_ctx ctx, int nrhs) {
 }
 
 size_t lqcd_packed_bytes(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs) {
-  if (!ctx || !valid_dtype(dtype) || !valid_sites(sites) || nrhs < 1) return 0;
-  return packed_elems(ctx, sites, nrhs) * (dtype == LQCD_C128 ? 16 : 8);
+  if (!ctx || !valid_storage(dtype) || !valid_sites(sites) || nrhs < 1) return 0;
+  return packed_elems(ctx, sites, nrhs) * elem_bytes(dtype);
 }
 
 static lqcd_status layout_common(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
                                  const void* in, void* out, void* stream, bool to_packed, const char* fn) {
   CHECK_CTX(ctx);
-  if (!valid_dtype(dtype) || !valid_sites(sites) || nrhs < 1 || nrhs > 256 || !in || !out)
+  if (!valid_storage(dtype) || !valid_sites(sites) || nrhs < 1 || nrhs > 256 || !in || !out)
     return set_error(LQCD_ERR_ARG, "%s: bad arguments", fn);
   const int sites_code = sites == LQCD_SITES_FULL ? 0 : 1;
   LQCD_CUDA(launch_spinor_layout(ctx->g, sites_code, nrhs, site_tile_log2(ctx, nrhs), to_packed,
-                                 dtype == LQCD_C128, in, out, (cudaStream_t)stream),
+                                 dtype == LQCD_C128, in, out, (cudaStream_t)stream, dtype == LQCD_BF16S),
             fn);
   return LQCD_OK;
 }
@@ -417,15 +456,18 @@ lqcd_status lqcd_apply_packed(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nr
   CHECK_CTX(ctx);
   lqcd_status st = check_ready(ctx, "lqcd_apply_packed");
   if (st != LQCD_OK) return st;
-  if ((op != LQCD_OP_FULL && op != LQCD_OP_SCHUR) || !valid_dtype(dtype) || nrhs < 1 || nrhs > 256 || !in ||
-      !out || in == out)
+  if ((op != LQCD_OP_FULL && op != LQCD_OP_SCHUR) || !valid_storage(dtype) || nrhs < 1 || nrhs > 256 || !in ||
+      !out || in == out || (dtype == LQCD_BF16S && nrhs > 128))
     return set_error(LQCD_ERR_ARG, "lqcd_apply_packed: bad arguments");
   void* tmp = nullptr;
+  const lqcd_dtype tmp_type = dtype == LQCD_C128 ? LQCD_C128 : LQCD_C64;
   if (op == LQCD_OP_SCHUR) {
     st = workspace(ctx, dtype == LQCD_C128 ? "schur_tmp64" : "schur_tmp32",
-                   lqcd_packed_bytes(ctx, dtype, LQCD_SITES_EVEN, nrhs), &tmp);
+                   lqcd_packed_bytes(ctx, tmp_type, LQCD_SITES_EVEN, nrhs), &tmp);
     if (st != LQCD_OK) return st;
   }
+  if (dtype == LQCD_BF16S)
+    return apply_operator_bf16in(ctx, op, nrhs, in, out, tmp, nullptr, (cudaStream_t)stream);
   return apply_operator(ctx, op, dtype == LQCD_C128, nrhs, in, out, tmp, nullptr, (cudaStream_t)stream);
 }
 
@@ -434,21 +476,21 @@ lqcd_status lqcd_apply(lqcd_ctx ctx, lqcd_op op, lqcd_dtype dtype, int nrhs, con
   CHECK_CTX(ctx);
   lqcd_status st = check_ready(ctx, "lqcd_apply");
   if (st != LQCD_OK) return st;
-  if ((op != LQCD_OP_FULL && op != LQCD_OP_SCHUR) || !valid_dtype(dtype) || nrhs < 1 || nrhs > 256 || !in ||
+  if ((op != LQCD_OP_FULL && op != LQCD_OP_SCHUR) || !valid_storage(dtype) || nrhs < 1 || nrhs > 256 || !in ||
       !out)
     return set_error(LQCD_ERR_ARG, "lqcd_apply: bad arguments");
   const lqcd_sites sites = op == LQCD_OP_FULL ? LQCD_SITES_FULL : LQCD_SITES_ODD;
-  const size_t bytes = lqcd_packed_bytes(ctx, dtype, sites, nrhs);
+  const lqcd_dtype out_type = dtype == LQCD_BF16S ? LQCD_C64 : dtype;   // BF16 input gives a complex64 result
   void *pin, *pout;
-  st = workspace(ctx, "apply_in", bytes, &pin);
+  st = workspace(ctx, "apply_in", lqcd_packed_bytes(ctx, dtype, sites, nrhs), &pin);
   if (st != LQCD_OK) return st;
-  st = workspace(ctx, "apply_out", bytes, &pout);
+  st = workspace(ctx, "apply_out", lqcd_packed_bytes(ctx, out_type, sites, nrhs), &pout);
   if (st != LQCD_OK) return st;
   st = lqcd_pack(ctx, dtype, sites, nrhs, in, pin, stream);
   if (st != LQCD_OK) return st;
   st = lqcd_apply_packed(ctx, op, dtype, nrhs, pin, pout, stream);
   if (st != LQCD_OK) return st;
-  return lqcd_unpack(ctx, dtype, sites, nrhs, pout, out, stream);
+  return lqcd_unpack(ctx, out_type, sites, nrhs, pout, out, stream);
 }
 
 lqcd_status lqcd_schur_prepare(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, const void* b, void* bhat_o,

@@ -73,6 +73,8 @@ bool is_device_pointer(const void* p);
 //   op FULL: in/out full blocks. op SCHUR: in/out odd blocks, tmp = even-half scratch.
 lqcd_status apply_operator(lqcd_ctx ctx, int op, bool f64, int nrhs, const void* in, void* out,
                            void* tmp, const int* skip, cudaStream_t stream);
+lqcd_status apply_operator_bf16in(lqcd_ctx ctx, int op, int nrhs, const void* in, void* out, void* tmp,
+                                  const int* skip, cudaStream_t stream);
 lqcd_status schur_prepare(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, void* bhat_o,
                           void* tmp_even, cudaStream_t stream);
 lqcd_status schur_reconstruct(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, const void* x_o,

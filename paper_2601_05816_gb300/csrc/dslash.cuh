@@ -24,6 +24,8 @@
 // from L1/L2: each spinor is used by its eight neighbours, which the lexicographic
 // thread order keeps within a few time slices, well inside the 129 MB L2.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace lqcd {
@@ -49,6 +51,7 @@ struct DslashArgs {
   const Real* blocks_inv;  // A(x)^{-1}, same layout
   Real self_scalar, post_scalar, c_hop;
   const int* skip;     // optional: return at once when *skip != 0
+  int loop_chunk;      // persistent variants: target sites per CTA (set by the launcher)
 };
 
 // NR complex numbers (NR consecutive rhs of one component).
@@ -95,6 +98,20 @@ __device__ __forceinline__ void mc_load(MC<double, 1>& a, const double2* p) {
   double2 v = __ldg(p);
   a.re[0] = v.x; a.im[0] = v.y;
 }
+// BF16-stored spinors (pairs re, im), converted to FP32 on load.
+__device__ __forceinline__ void mc_load(MC<float, 2>& a, const __nv_bfloat162* p) {
+  const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  __nv_bfloat162 b0, b1;
+  memcpy(&b0, &v.x, 4);
+  memcpy(&b1, &v.y, 4);
+  const float2 c0 = __bfloat1622float2(b0), c1 = __bfloat1622float2(b1);
+  a.re[0] = c0.x; a.im[0] = c0.y; a.re[1] = c1.x; a.im[1] = c1.y;
+}
+__device__ __forceinline__ void mc_load(MC<float, 1>& a, const __nv_bfloat162* p) {
+  const float2 c = __bfloat1622float2(__ldg(p));
+  a.re[0] = c.x; a.im[0] = c.y;
+}
+
 // Loads issued as volatile PTX: they keep their program order, so the link and
 // neighbour loads of one direction leave the SM back to back (one memory round
 // trip per direction) instead of being spread between the arithmetic.
@@ -205,9 +222,9 @@ __device__ __forceinline__ void hop_compute(const typename Cplx<Real>::T* u, con
 
 // One hopping direction with direct (register) loads of the link and the neighbour
 // (BATCH: as one batch of volatile loads).
-template <typename Real, int NR, int MU, int DIR, bool BATCH>
+template <typename Real, int NR, int MU, int DIR, bool BATCH, typename HIN>
 __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
-                                        const typename Cplx<Real>::T* hin, MC<Real, NR> acc[12]) {
+                                        const HIN* hin, MC<Real, NR> acc[12]) {
   using C = typename Cplx<Real>::T;
   const int nlex = neighbour_lex<MU, DIR>(a.g, c);
   const int ncb = nlex >> 1;
@@ -216,7 +233,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
   const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
   C u[9];
   MC<Real, NR> up[6], dn[6];
-  if (BATCH) {
+  if constexpr (BATCH) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = ldg_batch(lp + (int64_t)e * a.g.V);
 #pragma unroll
@@ -297,12 +314,10 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
   block_matvec<Real, NR>(m, x + 6, y + 6);
 }
 
-template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH>
-__global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
+// The whole operator on one target site for this thread's NR rhs.
+template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN>
+__device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site) {
   using C = typename Cplx<Real>::T;
-  if (a.skip != nullptr && *a.skip != 0) return;
-  const int site = blockIdx.x * blockDim.y + threadIdx.y;
-  if (site >= a.n_target) return;
   const int r0 = threadIdx.x * NR;
   int p, cb;
   if (a.full) {
@@ -320,15 +335,15 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
 
   if (a.hop) {
     const Coord c = site_coords(a.g, p, cb);
-    const C* hin = a.full ? a.hop_in + (1 - p) * a.half_elems : a.hop_in;
-    hop_dir<Real, NR, 0, +1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 0, -1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, +1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, -1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, +1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, -1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, +1, BATCH>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, -1, BATCH>(a, c, p, r0, hin, acc);
+    const HIN* hin = reinterpret_cast<const HIN*>(a.hop_in) + (a.full ? (1 - p) * a.half_elems : 0);
+    hop_dir<Real, NR, 0, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
 
   const int64_t base = a.full ? p * a.half_elems : 0;
   if (SELF != SELF_NONE) {
-    const C* sp = a.self_in + base;
+    const SIN* sp = reinterpret_cast<const SIN*>(a.self_in) + base;
     MC<Real, NR> s[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) mc_load(s[k], sp + a.lay.index(cb, k, r0));
@@ -377,6 +392,24 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   }
 }
 
+template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
+          typename SIN>
+__global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
+  if (a.skip != nullptr && *a.skip != 0) return;
+  if (!LOOP) {
+    const int site = blockIdx.x * blockDim.y + threadIdx.y;
+    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN>(a, site);
+    return;
+  }
+  // persistent CTAs: each walks one contiguous chunk of target sites, blockDim.y
+  // sites at a time, so the neighbour rows in x and y it loaded for the previous
+  // sites are still in L1 for the next ones
+  const int s0 = blockIdx.x * a.loop_chunk;
+  const int s1 = min(s0 + a.loop_chunk, a.n_target);
+  for (int site = s0 + threadIdx.y; site < s1; site += blockDim.y)
+    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN>(a, site);
+}
+
 // Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
 // nrhs/NR threads wide and threads/(nrhs/NR) sites tall) and a minimum number of
 // resident CTAs per SM (which caps the registers per thread). The autotuner
@@ -385,6 +418,7 @@ struct DslashVariant {
   int nr, threads, minb;
   int stages;  // 0: direct register loads; >= 2: cp.async pipeline depth (dslash_async.cuh)
   int batch;   // direct loads: 1 = each direction's loads issued as one batch
+  int loop;    // direct loads: 1 = persistent CTAs walking contiguous chunks of sites
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -396,12 +430,37 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
                           cudaStream_t stream);
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
-template <typename Real, int NR, int MAXT, int MINB, bool BATCH>
+template <typename Real, int NR, int SM, int PM, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
+          typename SIN>
+cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
+  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN>;
+  dim3 grid((a.n_target + block.y - 1) / block.y);
+  if (LOOP) {
+    // one wave of persistent CTAs, each with an equal contiguous chunk of sites
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x * block.y, 0);
+      if (per_sm < 1) per_sm = 1;
+    }
+    const int want = sms * per_sm;
+    const int rows = (int)grid.x;
+    const int per_cta = (rows + want - 1) / want;
+    a.loop_chunk = per_cta * (int)block.y;
+    grid.x = (a.n_target + a.loop_chunk - 1) / a.loop_chunk;
+  }
+  kern<<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real, int NR, int MAXT, int MINB, bool BATCH, bool LOOP = false,
+          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
-  dim3 grid((a.n_target + block.y - 1) / block.y);
-#define LQCD_DS(SM, PM) dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH><<<grid, block, 0, s>>>(a)
+#define LQCD_DS(SM, PM) return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN>(a, block, s)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -410,12 +469,15 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
   else if (self_mode == SELF_SCALAR && post_mode == POST_BLOCKINV) LQCD_DS(SELF_SCALAR, POST_BLOCKINV);
   else return cudaErrorInvalidValue;
 #undef LQCD_DS
-  return cudaGetLastError();
 }
 
 // Explicit instantiation of one variant's launcher in its own translation unit
 // (the variants compile in parallel).
-#define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB, BATCH) \
-  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, BATCH>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+#define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB, BATCH, LOOP) \
+  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, BATCH, LOOP>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+
+// FP32 arithmetic on BF16-stored inputs (hop input HIN, self-term input SIN), FP32 output.
+cudaError_t launch_dslash_bf16(const DslashArgs<float>& a, int self_mode, int post_mode, bool hop_bf16,
+                               cudaStream_t stream);
 
 }  // namespace lqcd

@@ -4,32 +4,32 @@
 namespace lqcd {
 
 namespace {
-// {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads), batched loads}
-const DslashVariant kF32[] = {{2, 128, 1, 0, 0}, {2, 128, 4, 0, 0}, {1, 128, 1, 0, 0}, {1, 128, 6, 0, 0}, {1, 256, 1, 0, 0}, {2, 256, 2, 0, 0}, {2, 128, 1, 2, 0}, {2, 128, 1, 3, 0}, {1, 128, 1, 3, 0}, {2, 128, 4, 0, 1}, {2, 128, 3, 0, 1}, {2, 64, 8, 0, 1}, {1, 128, 6, 0, 1}};
-const DslashVariant kF64[] = {{1, 128, 1, 0, 0}, {1, 128, 4, 0, 0}, {1, 256, 1, 0, 0}, {1, 64, 1, 0, 0}, {1, 128, 1, 2, 0}, {1, 128, 1, 3, 0}, {1, 128, 4, 0, 1}, {1, 64, 8, 0, 1}};
+// {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
+//  batched loads, persistent chunk loop}
+const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1}};
+const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
-extern template cudaError_t launch_dslash_variant<float, 2, 128, 1, false>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 1, 128, 1, false>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, false>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 1, 256, 1, false>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 1, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 1, 128, 1, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 1, 256, 1, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, false>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_async_variant<float, 2, 128, 1, 2>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_async_variant<float, 2, 128, 1, 3>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_async_variant<float, 1, 128, 1, 3>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, true>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 128, 3, true>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 64, 8, true>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, true>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 64, 1, false>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, true, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 64, 8, true, false>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, true, true>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 64, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_async_variant<double, 1, 128, 1, 2>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_async_variant<double, 1, 128, 1, 3>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, true>(const DslashArgs<double>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<double, 1, 64, 8, true>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, true, false>(const DslashArgs<double>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, true>(const DslashArgs<double>&, int, int, cudaStream_t);
 
 int dslash_variant_count(bool f64) { return f64 ? (int)(sizeof(kF64) / sizeof(kF64[0])) : (int)(sizeof(kF32) / sizeof(kF32[0])); }
 
@@ -50,22 +50,21 @@ int dslash_default_variant(bool f64, int nrhs) {
 template <>
 cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int post_mode, int variant,
                                  cudaStream_t s) {
-  if (!dslash_variant_ok(false, variant, a.lay.nrhs))
-    variant = dslash_default_variant(false, a.lay.nrhs);
+  if (!dslash_variant_ok(false, variant, a.lay.nrhs)) variant = dslash_default_variant(false, a.lay.nrhs);
   switch (variant) {
-    case 0: return launch_dslash_variant<float, 2, 128, 1, false>(a, self_mode, post_mode, s);
-    case 1: return launch_dslash_variant<float, 2, 128, 4, false>(a, self_mode, post_mode, s);
-    case 2: return launch_dslash_variant<float, 1, 128, 1, false>(a, self_mode, post_mode, s);
-    case 3: return launch_dslash_variant<float, 1, 128, 6, false>(a, self_mode, post_mode, s);
-    case 4: return launch_dslash_variant<float, 1, 256, 1, false>(a, self_mode, post_mode, s);
-    case 5: return launch_dslash_variant<float, 2, 256, 2, false>(a, self_mode, post_mode, s);
+    case 0: return launch_dslash_variant<float, 2, 128, 1, false, false>(a, self_mode, post_mode, s);
+    case 1: return launch_dslash_variant<float, 2, 128, 4, false, false>(a, self_mode, post_mode, s);
+    case 2: return launch_dslash_variant<float, 1, 128, 1, false, false>(a, self_mode, post_mode, s);
+    case 3: return launch_dslash_variant<float, 1, 128, 6, false, false>(a, self_mode, post_mode, s);
+    case 4: return launch_dslash_variant<float, 1, 256, 1, false, false>(a, self_mode, post_mode, s);
+    case 5: return launch_dslash_variant<float, 2, 256, 2, false, false>(a, self_mode, post_mode, s);
     case 6: return launch_dslash_async_variant<float, 2, 128, 1, 2>(a, self_mode, post_mode, s);
-    case 7: return launch_dslash_async_variant<float, 2, 128, 1, 3>(a, self_mode, post_mode, s);
-    case 8: return launch_dslash_async_variant<float, 1, 128, 1, 3>(a, self_mode, post_mode, s);
-    case 9: return launch_dslash_variant<float, 2, 128, 4, true>(a, self_mode, post_mode, s);
-    case 10: return launch_dslash_variant<float, 2, 128, 3, true>(a, self_mode, post_mode, s);
-    case 11: return launch_dslash_variant<float, 2, 64, 8, true>(a, self_mode, post_mode, s);
-    case 12: return launch_dslash_variant<float, 1, 128, 6, true>(a, self_mode, post_mode, s);
+    case 7: return launch_dslash_variant<float, 2, 128, 4, true, false>(a, self_mode, post_mode, s);
+    case 8: return launch_dslash_variant<float, 2, 64, 8, true, false>(a, self_mode, post_mode, s);
+    case 9: return launch_dslash_variant<float, 2, 128, 4, false, true>(a, self_mode, post_mode, s);
+    case 10: return launch_dslash_variant<float, 2, 128, 4, true, true>(a, self_mode, post_mode, s);
+    case 11: return launch_dslash_variant<float, 2, 256, 2, false, true>(a, self_mode, post_mode, s);
+    case 12: return launch_dslash_variant<float, 1, 128, 6, false, true>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -73,17 +72,15 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
 template <>
 cudaError_t launch_dslash<double>(const DslashArgs<double>& a, int self_mode, int post_mode, int variant,
                                  cudaStream_t s) {
-  if (!dslash_variant_ok(true, variant, a.lay.nrhs))
-    variant = dslash_default_variant(true, a.lay.nrhs);
+  if (!dslash_variant_ok(true, variant, a.lay.nrhs)) variant = dslash_default_variant(true, a.lay.nrhs);
   switch (variant) {
-    case 0: return launch_dslash_variant<double, 1, 128, 1, false>(a, self_mode, post_mode, s);
-    case 1: return launch_dslash_variant<double, 1, 128, 4, false>(a, self_mode, post_mode, s);
-    case 2: return launch_dslash_variant<double, 1, 256, 1, false>(a, self_mode, post_mode, s);
-    case 3: return launch_dslash_variant<double, 1, 64, 1, false>(a, self_mode, post_mode, s);
+    case 0: return launch_dslash_variant<double, 1, 128, 1, false, false>(a, self_mode, post_mode, s);
+    case 1: return launch_dslash_variant<double, 1, 128, 4, false, false>(a, self_mode, post_mode, s);
+    case 2: return launch_dslash_variant<double, 1, 256, 1, false, false>(a, self_mode, post_mode, s);
+    case 3: return launch_dslash_variant<double, 1, 64, 1, false, false>(a, self_mode, post_mode, s);
     case 4: return launch_dslash_async_variant<double, 1, 128, 1, 2>(a, self_mode, post_mode, s);
-    case 5: return launch_dslash_async_variant<double, 1, 128, 1, 3>(a, self_mode, post_mode, s);
-    case 6: return launch_dslash_variant<double, 1, 128, 4, true>(a, self_mode, post_mode, s);
-    case 7: return launch_dslash_variant<double, 1, 64, 8, true>(a, self_mode, post_mode, s);
+    case 5: return launch_dslash_variant<double, 1, 128, 4, true, false>(a, self_mode, post_mode, s);
+    case 6: return launch_dslash_variant<double, 1, 128, 4, false, true>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }

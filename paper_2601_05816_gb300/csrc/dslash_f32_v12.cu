@@ -1,6 +1,6 @@
-// FP32 hopping-kernel variant 12: 1 rhs per thread, 128 threads per CTA, >= 6 CTA(s) per SM, batched loads.
+// FP32 hopping-kernel variant 12: 1 rhs per thread, 128 threads per CTA, >= 6 CTA(s) per SM, persistent CTAs over contiguous site chunks.
 #include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_VARIANT_TU(float, 1, 128, 6, true)
+LQCD_DSLASH_VARIANT_TU(float, 1, 128, 6, false, true)
 }  // namespace lqcd

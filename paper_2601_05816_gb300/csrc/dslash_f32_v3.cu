@@ -2,5 +2,5 @@
 #include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_VARIANT_TU(float, 1, 128, 6, false)
+LQCD_DSLASH_VARIANT_TU(float, 1, 128, 6, false, false)
 }  // namespace lqcd

@@ -1,6 +1,6 @@
-// FP32 hopping-kernel variant 7: cp.async pipeline of 3 stages, 2 rhs per thread, 128 threads per CTA.
-#include "dslash_async.cuh"
+// FP32 hopping-kernel variant 7: 2 rhs per thread, 128 threads per CTA, >= 4 CTA(s) per SM, batched loads.
+#include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_ASYNC_VARIANT_TU(float, 2, 128, 1, 3)
+LQCD_DSLASH_VARIANT_TU(float, 2, 128, 4, true, false)
 }  // namespace lqcd

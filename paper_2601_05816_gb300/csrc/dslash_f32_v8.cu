@@ -1,6 +1,6 @@
-// FP32 hopping-kernel variant 8: cp.async pipeline of 3 stages, 1 rhs per thread, 128 threads per CTA.
-#include "dslash_async.cuh"
+// FP32 hopping-kernel variant 8: 2 rhs per thread, 64 threads per CTA, >= 8 CTA(s) per SM, batched loads.
+#include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_ASYNC_VARIANT_TU(float, 1, 128, 1, 3)
+LQCD_DSLASH_VARIANT_TU(float, 2, 64, 8, true, false)
 }  // namespace lqcd

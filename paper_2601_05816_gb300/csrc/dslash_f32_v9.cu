@@ -1,6 +1,6 @@
-// FP32 hopping-kernel variant 9: 2 rhs per thread, 128 threads per CTA, >= 4 CTA(s) per SM, batched loads.
+// FP32 hopping-kernel variant 9: 2 rhs per thread, 128 threads per CTA, >= 4 CTA(s) per SM, persistent CTAs over contiguous site chunks.
 #include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_VARIANT_TU(float, 2, 128, 4, true)
+LQCD_DSLASH_VARIANT_TU(float, 2, 128, 4, false, true)
 }  // namespace lqcd

@@ -2,5 +2,5 @@
 #include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_VARIANT_TU(double, 1, 128, 4, false)
+LQCD_DSLASH_VARIANT_TU(double, 1, 128, 4, false, false)
 }  // namespace lqcd

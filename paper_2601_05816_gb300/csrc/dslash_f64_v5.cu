@@ -1,6 +1,6 @@
-// FP64 hopping-kernel variant 5: cp.async pipeline of 3 stages, 1 rhs per thread, 128 threads per CTA.
-#include "dslash_async.cuh"
+// FP64 hopping-kernel variant 5: 1 rhs per thread, 128 threads per CTA, >= 4 CTA(s) per SM, batched loads.
+#include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_ASYNC_VARIANT_TU(double, 1, 128, 1, 3)
+LQCD_DSLASH_VARIANT_TU(double, 1, 128, 4, true, false)
 }  // namespace lqcd

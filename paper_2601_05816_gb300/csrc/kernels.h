@@ -1,5 +1,6 @@
 // Internal launcher declarations shared by the library's translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -8,8 +9,9 @@
 namespace lqcd {
 
 // pack.cu
+// bf16: packed side BF16 pairs, canonical side complex64 (f64 ignored).
 cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, bool to_packed,
-                                 bool f64, const void* in, void* out, cudaStream_t stream);
+                                 bool f64, const void* in, void* out, cudaStream_t stream, bool bf16 = false);
 cudaError_t launch_gauge_pack(const Geom& g, int time_bc, const void* U, void* l64, void* l32,
                               cudaStream_t stream);
 
@@ -39,10 +41,13 @@ BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
 // [plan.blocks][nvec + 1][nrhs]. skip: optional device flag (return when set).
 //   oscale: optional device double [nrhs]; the updated w is multiplied by it before the store
 //   (dots and norm refer to the unscaled w). With neither dots nor norm no reduction runs.
+//   basis_bf16: basis stored as BF16 pairs (FP32 arithmetic, w in FP32; needs nrhs <= 32);
+//   wout: optional, the scaled updated w is stored there (in the basis storage type) instead of in w.
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
-                           cudaStream_t stream, const double* oscale = nullptr);
+                           cudaStream_t stream, const double* oscale = nullptr, bool basis_bf16 = false,
+                           void* wout = nullptr);
 
 // r = b - t (all FP64) with out[0][r] = ||r||^2.
 cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
@@ -50,16 +55,16 @@ cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, cons
 // ||v||^2 per rhs, out[0][r]; v in FP64 or FP32.
 cudaError_t launch_norm2(bool f64, const BlasPlan& plan, int64_t n, const void* v, void* partials,
                          void* out, cudaStream_t stream);
-// dst[e] = (dst precision) (src[e] * scale[r]); src FP64, dst FP64 or FP32.
+// dst[e] = (dst precision) (src[e] * scale[r]); src FP64, dst FP64, FP32 or BF16 pairs.
 cudaError_t launch_scale_convert(bool dst_f64, int64_t n, int nrhs, const void* src,
-                                 const double* scale, void* dst, cudaStream_t stream);
+                                 const double* scale, void* dst, cudaStream_t stream, bool dst_bf16 = false);
 // v[e] *= scale[r] in place (v FP64 or FP32).
 cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const double* scale,
                                  const int* skip, cudaStream_t stream);
 // x[e] += sum_{i < *kmax} y[i][r] v_i[e]; x FP64, basis FP64 or FP32 (sum in basis precision).
 cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
                             int64_t vstride, const void* y, const int* kmax, void* x,
-                            cudaStream_t stream);
+                            cudaStream_t stream, bool basis_bf16 = false);
 // Widen / narrow copies between FP64 and FP32 packed blocks.
 cudaError_t launch_convert(bool to_f64, int64_t n, const void* src, void* dst, cudaStream_t stream);
 

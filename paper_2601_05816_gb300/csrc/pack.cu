@@ -33,9 +33,15 @@ __device__ __forceinline__ int64_t canonical_site(const Geom& g, int sites, int6
   return i;  // one parity: canonical order is cb order
 }
 
-template <typename C, bool TO_PACKED>
+__device__ __forceinline__ float2 cvt(__nv_bfloat162 v, float2*) { return __bfloat1622float2(v); }
+__device__ __forceinline__ __nv_bfloat162 cvt(float2 v, __nv_bfloat162*) { return __float22bfloat162_rn(v); }
+template <typename C>
+__device__ __forceinline__ C cvt(C v, C*) { return v; }
+
+// Canonical <-> packed; CIN/COUT differ for the BF16 packed storage (complex64 canonical).
+template <typename CIN, typename COUT, bool TO_PACKED>
 __global__ void spinor_layout_kernel(Geom g, int sites, int nrhs, int log_s, int64_t n_sites,
-                                     const C* __restrict__ in, C* __restrict__ out) {
+                                     const CIN* __restrict__ in, COUT* __restrict__ out) {
   const int64_t total = n_sites * 12 * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -43,31 +49,39 @@ __global__ void spinor_layout_kernel(Geom g, int sites, int nrhs, int log_s, int
     decode_packed(e, nrhs, log_s, i, c, r);
     const int64_t cs = canonical_site(g, sites, i);
     const int64_t ce = ((int64_t)r * n_sites + cs) * 12 + c;
-    if (TO_PACKED) out[e] = in[ce];
-    else out[ce] = in[e];
+    if (TO_PACKED) out[e] = cvt(in[ce], (COUT*)nullptr);
+    else out[ce] = cvt(in[e], (COUT*)nullptr);
   }
 }
 
 cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, bool to_packed,
-                                 bool f64, const void* in, void* out, cudaStream_t stream) {
+                                 bool f64, const void* in, void* out, cudaStream_t stream, bool bf16) {
   const int64_t n_sites = sites == 0 ? g.V : g.Vh;
   const int64_t total = n_sites * 12 * nrhs;
   const int threads = 256;
   int64_t blocks64 = (total + threads - 1) / threads;
   const int blocks = (int)(blocks64 > 65535 * 16 ? 65535 * 16 : blocks64);
-  if (f64) {
+  using bf2 = __nv_bfloat162;
+  if (bf16) {
     if (to_packed)
-      spinor_layout_kernel<double2, true><<<blocks, threads, 0, stream>>>(
+      spinor_layout_kernel<float2, bf2, true><<<blocks, threads, 0, stream>>>(
+          g, sites, nrhs, log_s, n_sites, (const float2*)in, (bf2*)out);
+    else
+      spinor_layout_kernel<bf2, float2, false><<<blocks, threads, 0, stream>>>(
+          g, sites, nrhs, log_s, n_sites, (const bf2*)in, (float2*)out);
+  } else if (f64) {
+    if (to_packed)
+      spinor_layout_kernel<double2, double2, true><<<blocks, threads, 0, stream>>>(
           g, sites, nrhs, log_s, n_sites, (const double2*)in, (double2*)out);
     else
-      spinor_layout_kernel<double2, false><<<blocks, threads, 0, stream>>>(
+      spinor_layout_kernel<double2, double2, false><<<blocks, threads, 0, stream>>>(
           g, sites, nrhs, log_s, n_sites, (const double2*)in, (double2*)out);
   } else {
     if (to_packed)
-      spinor_layout_kernel<float2, true><<<blocks, threads, 0, stream>>>(
+      spinor_layout_kernel<float2, float2, true><<<blocks, threads, 0, stream>>>(
           g, sites, nrhs, log_s, n_sites, (const float2*)in, (float2*)out);
     else
-      spinor_layout_kernel<float2, false><<<blocks, threads, 0, stream>>>(
+      spinor_layout_kernel<float2, float2, false><<<blocks, threads, 0, stream>>>(
           g, sites, nrhs, log_s, n_sites, (const float2*)in, (float2*)out);
   }
   return cudaGetLastError();

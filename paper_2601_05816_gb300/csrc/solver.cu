@@ -189,6 +189,8 @@ cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream) {
 
 struct SolveBufs {
   bool f64_inner;
+  bool bf16;            // basis stored as BF16 pairs, FP32 arithmetic, new vector in w32
+  void* w32;            // FP32 buffer of the vector being orthogonalised (bf16 mode)
   int nrhs, m;
   int64_t n_sys;        // complex elements of the system vector
   size_t inner_bytes;   // bytes per inner basis vector
@@ -213,19 +215,20 @@ struct SolveBufs {
 static lqcd_status arnoldi_ortho(const SolveBufs& b, int j, bool reorth, cudaEvent_t ev_gs_end, cudaStream_t s) {
   const int nvec = j + 1;
   char* base = (char*)b.basis;
-  void* w = base + (size_t)(j + 1) * b.inner_bytes;
+  void* next = base + (size_t)(j + 1) * b.inner_bytes;
+  void* w = b.bf16 ? b.w32 : next;
   const int64_t vstride = b.n_sys;
   const int* skip = b.st.all_done;
   LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, nullptr, false, true,
-                           false, b.partials, b.h1, skip, s),
+                           false, b.partials, b.h1, skip, s, nullptr, b.bf16),
             "gs dots");
   if (reorth) {
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, true,
-                             true, b.partials, b.h2, skip, s),
+                             true, b.partials, b.h2, skip, s, nullptr, b.bf16),
               "gs update+dots+norm");
     LQCD_CUDA(launch_givens(b.st, j, b.h1, b.h2, b.h2, true, s), "givens");
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h2, true, false,
-                             false, b.partials, nullptr, skip, s, b.st.scale),
+                             false, b.partials, nullptr, skip, s, b.st.scale, b.bf16, b.bf16 ? next : nullptr),
               "gs update+scale");
   } else {
     LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.h1, true, false,
@@ -252,18 +255,27 @@ struct Profile {
 // Schur: (120 b + 432) s per odd site with clover, (120 b + 288) s without
 // (s = bytes per real; spinors read/written once per pass, 18 reals per link,
 // 72 reals per site block).
-static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int nrhs) {
+static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int nrhs, bool bf16 = false) {
   const double s = f64 ? 8.0 : 4.0;
   const bool clover = ctx->c_sw != 0.0;
-  if (op == LQCD_OP_FULL) return (double)ctx->g.V * (48.0 * nrhs + (clover ? 144.0 : 72.0)) * s;
-  return (double)ctx->g.Vh * (120.0 * nrhs + (clover ? 432.0 : 288.0)) * s;
+  const double fixed = op == LQCD_OP_FULL ? (clover ? 144.0 : 72.0) : (clover ? 432.0 : 288.0);
+  if (bf16) {  // BF16 input read (2 bytes per real), FP32 intermediate and output
+    if (op == LQCD_OP_FULL) return (double)ctx->g.V * (24.0 * nrhs * 2 + 24.0 * nrhs * 4 + fixed * 4);
+    return (double)ctx->g.Vh * (2 * 24.0 * nrhs * 2 + 3 * 24.0 * nrhs * 4 + fixed * 4);
+  }
+  if (op == LQCD_OP_FULL) return (double)ctx->g.V * (48.0 * nrhs + fixed) * s;
+  return (double)ctx->g.Vh * (120.0 * nrhs + fixed) * s;
 }
 
 // Algorithmic bytes of the Gram-Schmidt step with nvec basis vectors on n complex
 // elements: the dot pass reads nvec + 1 vectors; each update pass reads nvec + 1
 // and writes 1 (CGS2: two updates, the second one normalising; CGS1: one update
 // and a separate normalisation that reads and writes w once more).
-static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, bool reorth) {
+static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, bool reorth, bool bf16 = false) {
+  if (bf16) {  // BF16 basis (4 bytes per complex), FP32 w; the last pass writes the BF16 basis vector
+    const double vb = (double)n * 4.0, vw = (double)n * 8.0;
+    return (nvec * vb + vw) + (nvec * vb + 2 * vw) + (nvec * vb + vw + vb);
+  }
   const double v = (double)n * (f64 ? 16.0 : 8.0);
   const double dots = (nvec + 1) * v, upd = (nvec + 2) * v;
   return reorth ? dots + 2 * upd : dots + upd + 2 * v;
@@ -276,7 +288,8 @@ static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bo
     void* vj = base + (size_t)j * b.inner_bytes;
     void* w = base + (size_t)(j + 1) * b.inner_bytes;
     if (prof->on) LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 0], s), "event");
-    lqcd_status st = apply_operator(ctx, op, b.f64_inner, b.nrhs, vj, w, b.tmp_even_in, b.st.all_done, s);
+    lqcd_status st = b.bf16 ? apply_operator_bf16in(ctx, op, b.nrhs, vj, b.w32, b.tmp_even_in, b.st.all_done, s)
+                            : apply_operator(ctx, op, b.f64_inner, b.nrhs, vj, w, b.tmp_even_in, b.st.all_done, s);
     if (st != LQCD_OK) return st;
     if (prof->on) {
       LQCD_CUDA(cudaEventRecord(prof->ev[4 * j + 1], s), "event");
@@ -295,8 +308,8 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
   // profiled cycle is launched kernel by kernel.
   if (!use_graph || prof->on) return run_cycle_direct(ctx, b, op, reorth, prof, s);
   char key[256];
-  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%p/%p/%p/%lld", op, (int)b.f64_inner, b.nrhs, b.m, (int)reorth,
-           b.basis, b.partials, (void*)b.st.H, (long long)b.n_sys);
+  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%d/%p/%p/%p/%p/%lld", op, (int)b.f64_inner, (int)b.bf16, b.nrhs, b.m,
+           (int)reorth, b.basis, b.w32, b.partials, (void*)b.st.H, (long long)b.n_sys);
   if (ctx->cycle.exec == nullptr || ctx->cycle.key != key) {
     if (ctx->cycle.exec) {
       cudaGraphExecDestroy(ctx->cycle.exec);
@@ -332,7 +345,7 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
 
 // Accumulate the event times of the steps that ran (j < kmax: later steps were
 // skipped on the device once every rhs had finished its cycle).
-static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n, bool f64, bool reorth) {
+static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n, bool f64, bool reorth, bool bf16) {
   if (!prof->on) return;
   for (int j = 0; j < prof->used && j < kmax; ++j) {
     float a = 0.f, c = 0.f;
@@ -344,7 +357,7 @@ static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n,
     if (cudaEventElapsedTime(&c, prof->ev[4 * j + 2], prof->ev[4 * j + 3]) == cudaSuccess) {
       prof->gs_ms += c;
       prof->gs_n += 1;
-      prof->gs_bytes += gs_algorithmic_bytes(n, j + 1, f64, reorth);
+      prof->gs_bytes += gs_algorithmic_bytes(n, j + 1, f64, reorth, bf16);
     }
   }
   prof->used = 0;
@@ -369,11 +382,14 @@ extern "C" {
 lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs, int nvec,
                                const void* basis, void* w, void* h, void* hnorm, int reorth, void* stream) {
   if (!ctx) return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: null context");
-  if ((dtype != LQCD_C64 && dtype != LQCD_C128) || nrhs < 1 || nrhs > 256 || nvec < 1 || nvec > 64 || !basis ||
-      !w || !h || !hnorm || (sites != LQCD_SITES_FULL && sites != LQCD_SITES_EVEN && sites != LQCD_SITES_ODD))
+  if ((dtype != LQCD_C64 && dtype != LQCD_C128 && dtype != LQCD_BF16S) || nrhs < 1 || nrhs > 256 || nvec < 1 ||
+      nvec > 64 || !basis || !w || !h || !hnorm ||
+      (sites != LQCD_SITES_FULL && sites != LQCD_SITES_EVEN && sites != LQCD_SITES_ODD) ||
+      (dtype == LQCD_BF16S && nrhs > 32))
     return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = dtype == LQCD_C128;
+  const bool bf16 = dtype == LQCD_BF16S;
   const int64_t n = (int64_t)packed_elems(ctx, sites, nrhs);
   BlasPlan plan = blas_plan(n, nrhs, ctx->num_sms);
   void *partials, *h1, *h2, *hn;
@@ -383,15 +399,19 @@ lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites,
   if (st == LQCD_OK) st = workspace(ctx, "ortho_h2", hb, &h2);
   if (st == LQCD_OK) st = workspace(ctx, "ortho_hn", hb, &hn);
   if (st != LQCD_OK) return st;
-  LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, nullptr, false, true, false, partials, h1, nullptr, s),
+  LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, nullptr, false, true, false, partials, h1, nullptr, s,
+                           nullptr, bf16),
             "gs dots");
   if (reorth) {
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, true, false, partials, h2, nullptr, s),
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, true, false, partials, h2, nullptr, s,
+                             nullptr, bf16),
               "gs update+dots");
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h2, true, false, true, partials, hn, nullptr, s),
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h2, true, false, true, partials, hn, nullptr, s,
+                             nullptr, bf16),
               "gs update+norm");
   } else {
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, false, true, partials, hn, nullptr, s),
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, false, true, partials, hn, nullptr, s,
+                             nullptr, bf16),
               "gs update+norm");
   }
   const int q = nvec * nrhs > nrhs ? nvec * nrhs : nrhs;
@@ -410,13 +430,16 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     return set_error(LQCD_ERR_STATE, "lqcd_solve: set_gauge and set_clover must be called first");
   if (nrhs < 1 || nrhs > 64 || P->restart_len < 1 || P->restart_len > 64 || P->max_restarts < 1 ||
       !(P->tol > 0.0) || (P->op != LQCD_OP_FULL && P->op != LQCD_OP_SCHUR) ||
-      (P->precision != LQCD_C64 && P->precision != LQCD_C128))
-    return set_error(LQCD_ERR_ARG, "lqcd_solve: bad parameters (nrhs 1..64, restart_len 1..64, tol > 0)");
+      (P->precision != LQCD_C64 && P->precision != LQCD_C128 && P->precision != LQCD_BF16S) ||
+      (P->precision == LQCD_BF16S && nrhs > 32))
+    return set_error(LQCD_ERR_ARG,
+                     "lqcd_solve: bad parameters (nrhs 1..64, 1..32 for BF16 storage, restart_len 1..64, tol > 0)");
   cudaStream_t s = (cudaStream_t)stream;
   const bool eo = P->op == LQCD_OP_SCHUR;
   const bool f64_inner = P->precision == LQCD_C128;
+  const bool bf16 = P->precision == LQCD_BF16S;
   const int m = P->restart_len;
-  const bool reorth = P->reorth != 0;
+  const bool reorth = P->reorth != 0 || bf16;
   const double inner_tol = P->inner_tol > 0.0 ? P->inner_tol : (f64_inner ? 0.0 : 1e-5);
   long long nl = 0;  // kernel launches of this call
   const int64_t n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
@@ -440,11 +463,14 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
   }
   SolveBufs B;
   B.f64_inner = f64_inner;
+  B.bf16 = bf16;
+  B.w32 = nullptr;
   B.nrhs = nrhs;
   B.m = m;
   B.n_sys = n_sys;
-  B.inner_bytes = (size_t)n_sys * (f64_inner ? sizeof(double2) : sizeof(float2));
+  B.inner_bytes = (size_t)n_sys * (f64_inner ? sizeof(double2) : (bf16 ? sizeof(__nv_bfloat162) : sizeof(float2)));
   if ((st = workspace(ctx, "solve_basis", B.inner_bytes * (m + 1), &B.basis)) != LQCD_OK) return st;
+  if (bf16 && (st = workspace(ctx, "solve_w32", (size_t)n_sys * sizeof(float2), &B.w32)) != LQCD_OK) return st;
   B.tmp_even_in = nullptr;
   if (eo) {
     if (f64_inner) B.tmp_even_in = tmp64;
@@ -535,7 +561,7 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
   // ---------------- restarts
   std::vector<int> iters(nrhs, 0);
   std::vector<double> relres(nrhs, 0.0);
-  const double op_bytes_inner = op_algorithmic_bytes(ctx, P->op, f64_inner, nrhs);
+  const double op_bytes_inner = op_algorithmic_bytes(ctx, P->op, f64_inner, nrhs, bf16);
   int restarts = 0;
   lqcd_status result = LQCD_NOT_CONVERGED;
   bool pending_k = false;
@@ -552,7 +578,7 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
         iters[r] += hs->kcycle[r];
         kmax = std::max(kmax, hs->kcycle[r]);
       }
-      collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth);
+      collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth, bf16);
     }
     pending_k = false;
     int n_active = 0;
@@ -580,10 +606,10 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     LQCD_CUDA(cudaMemcpyAsync(B.st.thr, hs->thr, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
     LQCD_CUDA(cudaMemcpyAsync(d_beta0, hs->beta0, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
     LQCD_CUDA(launch_cycle_init(B.st, d_beta0, s), "cycle init");
-    LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, s), "v0");
+    LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, s, bf16), "v0");
     if ((st = run_cycle(ctx, B, P->op, reorth, P->use_graph != 0, &prof, s)) != LQCD_OK) return st;
     LQCD_CUDA(launch_backsub(B.st, s), "backsub");
-    LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, s),
+    LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, s, bf16),
               "update x");
     // cycle_init, v0, per step (operator, Gram-Schmidt passes with their reductions, givens,
     // normalisation), backsub, update

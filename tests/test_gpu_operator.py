@@ -285,3 +285,81 @@ def test_every_kernel_variant_and_tuner(dtype):
     assert lat.load_tuning(path)
     for (d, n, o) in keys:
         assert lat.kernel_variant(d, n, o) == saved[f"{d},{n},{o}"]
+
+
+def _bf16_round(a):
+    """Round a complex array to BF16 real and imaginary parts (round to nearest even), back to complex128."""
+    t = torch.from_numpy(np.ascontiguousarray(a)).to(torch.complex64)
+    r = torch.view_as_real(t).to(torch.bfloat16).to(torch.float32)
+    return torch.view_as_complex(r.contiguous()).numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("nrhs", [1, 6, 16])
+@pytest.mark.parametrize("sites", [lq.SITES_FULL, lq.SITES_ODD])
+def test_bf16_pack_roundtrip_rounds_like_torch(nrhs, sites):
+    lat, *_ = setup((8, 2, 6, 4), "exp", 0.5, 0.05, 1.3, 101)
+    n_sites = lat.V if sites == lq.SITES_FULL else lat.V // 2
+    g = torch.Generator(device="cpu").manual_seed(7 + nrhs)
+    src = torch.randn((nrhs, n_sites, 4, 3), dtype=torch.complex64, generator=g)
+    packed = lat.packed_empty(lq.BF16S, sites, nrhs)
+    back = torch.empty_like(src).cuda()
+    lat.pack(sites, nrhs, src.cuda(), packed, dtype=lq.BF16S)
+    lat.unpack(sites, nrhs, packed, back, dtype=lq.BF16S)
+    torch.cuda.synchronize()
+    expect = _bf16_round(src.numpy()).astype(np.complex64)
+    assert np.array_equal(back.cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("op", [lq.OP_FULL, lq.OP_SCHUR])
+@pytest.mark.parametrize("nrhs", [3, 16])
+def test_bf16_storage_operator(case, op, nrhs):
+    """BF16-stored input, FP32 arithmetic: equals the oracle applied to the BF16-rounded input."""
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    psi = syn.gaussian_spinors(dims, nrhs, 600 + nrhs)
+    src = psi if op == lq.OP_FULL else oracle.split_parity(psi, 1)
+    src_r = _bf16_round(src)
+    ref = (oracle.apply_D(U, src_r, m0, C if c_sw else None) if op == lq.OP_FULL
+           else oracle.apply_schur(U, A, Ainv, src_r))
+    d_in = torch.from_numpy(np.ascontiguousarray(src)).to(torch.complex64).cuda()
+    d_out = torch.empty_like(d_in)
+    lat.apply(op, nrhs, d_in, d_out, dtype=lq.BF16S)
+    torch.cuda.synchronize()
+    assert relerr(d_out.cpu().numpy(), ref) < TOL[lq.C64]
+
+
+@pytest.mark.parametrize("nvec,nrhs", [(5, 3), (17, 12), (32, 16)])
+def test_orthogonalise_bf16_basis(nvec, nrhs):
+    """BF16-stored basis, complex64 w: h = V^H w and w' = (1 - V V^H) w with V the BF16-rounded basis."""
+    lat, *_ = setup((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0, 101)
+    n_sites = lat.V // 2
+    rng = np.random.default_rng(nvec * 7 + nrhs)
+    N = n_sites * 12
+    Vb = np.empty((nvec, nrhs, N), complex)
+    for r in range(nrhs):
+        Z = rng.standard_normal((N, nvec)) + 1j * rng.standard_normal((N, nvec))
+        Q, _ = np.linalg.qr(Z)
+        Vb[:, r, :] = Q.T
+    Vb = _bf16_round(Vb)
+    w = (rng.standard_normal((nrhs, N)) + 1j * rng.standard_normal((nrhs, N))).astype(np.complex64).astype(complex)
+    # the projection with a not exactly orthonormal basis, as the kernels compute it (CGS2)
+    h1 = np.einsum("irn,rn->ir", Vb.conj(), w)
+    w1 = w - np.einsum("irn,ir->rn", Vb, h1)
+    h2 = np.einsum("irn,rn->ir", Vb.conj(), w1)
+    w2 = w1 - np.einsum("irn,ir->rn", Vb, h2)
+    basis = torch.cat([lat.packed_empty(lq.BF16S, lq.SITES_ODD, nrhs) for _ in range(nvec)])
+    nb = basis.numel() // nvec
+    for i in range(nvec):
+        src = torch.from_numpy(Vb[i].reshape(nrhs, n_sites, 4, 3)).to(torch.complex64).cuda()
+        lat.pack(lq.SITES_ODD, nrhs, src, basis[i * nb:(i + 1) * nb], dtype=lq.BF16S)
+    wp = lat.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
+    lat.pack(lq.SITES_ODD, nrhs, dev(w.reshape(nrhs, n_sites, 4, 3), lq.C64), wp)
+    h = torch.empty((nvec, nrhs), dtype=torch.complex128, device="cuda")
+    hn = torch.empty(nrhs, dtype=torch.float64, device="cuda")
+    lat.orthogonalise(lq.SITES_ODD, nrhs, nvec, basis, wp, h, hn, reorth=True, dtype=lq.BF16S)
+    wout = torch.empty((nrhs, n_sites, 4, 3), dtype=torch.complex64, device="cuda")
+    lat.unpack(lq.SITES_ODD, nrhs, wp, wout)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(h.cpu().numpy() - (h1 + h2))) < 2e-5 * np.max(np.abs(h1))
+    assert relerr(wout.cpu().numpy().reshape(nrhs, N), w2) < 1e-5

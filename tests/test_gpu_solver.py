@@ -132,3 +132,21 @@ def test_not_converged_and_nonfinite_status():
         lat.solve(b, x, 1, op=lq.OP_FULL, precision=lq.C128)
     assert ei.value.status == lq.ERR_NONFINITE
     lat.close()
+
+
+@pytest.mark.parametrize("op", [lq.OP_SCHUR, lq.OP_FULL])
+def test_bf16_basis_solve(op):
+    """FP32 Arnoldi with the basis stored in BF16 inside FP64 restarts still reaches 1e-10."""
+    dims = (8, 8, 8, 8)
+    m0, c_sw = -0.2, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1001)
+    b = syn.gaussian_spinors(dims, 4, 1003)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    x = np.zeros_like(b)
+    res = lat.solve(b, x, 4, op=op, precision=lq.BF16S, restart_len=32, tol=1e-10)
+    assert res.status == lq.OK, res
+    rel = oracle_relres(U, m0, c_sw, b, x)
+    assert np.all(rel <= 1e-10), rel
+    lat.close()
