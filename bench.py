@@ -537,6 +537,8 @@ def main():
     ap.add_argument("--max-restarts", type=int, default=500)
     ap.add_argument("--precision", default="c64", choices=["c64", "bf16"],
                     help="inner Arnoldi basis storage of the timed solve (FP32 arithmetic either way)")
+    ap.add_argument("--nvec", type=int, default=None,
+                    help="ortho workload: basis size of the timed CGS2 step (default 16)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
     args = ap.parse_args()
@@ -545,6 +547,9 @@ def main():
         w["m0_prescribed"] = w["m0"]
         w["m0"] = args.m0
         w["name"] += f" (companion run, m0 {args.m0} instead of {w['m0_prescribed']})"
+    if args.nvec is not None and w.get("kind") == "ortho":
+        w["name"] = w["name"].replace(f"nvec={w['nvec']}", f"nvec={args.nvec}")
+        w["nvec"] = args.nvec
     if args.impl == "reference":
         run_reference(args, w)
     elif w.get("kind") in ("apply", "ortho"):

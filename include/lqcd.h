@@ -186,7 +186,8 @@ lqcd_status lqcd_schur_reconstruct(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
  * h_norm = ||w||. basis: device, nvec packed blocks back to back (each
  * lqcd_packed_bytes(dtype, sites, nrhs) bytes); w: device packed block, updated
  * in place. h: device, complex128 [nvec][nrhs]; hnorm: device, double [nrhs].
- * dtype LQCD_BF16S: BF16 basis, complex64 w, FP32 arithmetic (nrhs <= 32).
+ * dtype LQCD_BF16S: BF16 basis, complex64 w, FP32 arithmetic (nrhs <= 32, or even
+ * nrhs <= 64).
  * nvec: 1..129. Dot products accumulate per thread in the vector precision and
  * across threads in FP64, in a fixed order (deterministic). */
 lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs,
@@ -197,7 +198,8 @@ typedef struct {
   int op;             /* LQCD_OP_FULL: GMRES on D; LQCD_OP_SCHUR: on S, x_e reconstructed */
   int precision;      /* LQCD_C128: FP64 Arnoldi; LQCD_C64: FP32 operator and Arnoldi
                          inside FP64 restarts (iterative refinement); LQCD_BF16S: as C64
-                         with the Arnoldi basis stored in BF16 (CGS2 always, nrhs <= 32) */
+                         with the Arnoldi basis stored in BF16 (CGS2 always; nrhs <= 32
+                         or even nrhs <= 64) */
   int restart_len;    /* m, 1..64 */
   int max_restarts;   /* >= 1 */
   double tol;         /* stop when ||b - D x|| <= tol ||b|| (true residual, per rhs) */
@@ -238,6 +240,21 @@ typedef struct {
  * stats: host, may be NULL. nrhs: 1..64. */
 lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* params, int nrhs,
                        const void* b, void* x, lqcd_solve_stats* stats, void* stream);
+
+/* Batched GMRES over several lattices of uneven size (one lattice context per
+ * entry, distinct contexts): the solve of lqcd_solve for every lattice i with
+ * params[i], nrhs[i] rhs, b[i] and x[i] (host or device, canonical complex128),
+ * stats[i] (may be NULL). Each restart round synchronises `stream` once for all
+ * lattices, retires the lattices whose rhs all meet their tolerance, and runs the
+ * restart cycles of all remaining lattices as one captured CUDA graph whose
+ * branches (one per lattice, on side streams) execute concurrently; the graph is
+ * re-captured only when the set of running lattices changes. Per-rhs retirement
+ * inside a cycle works as in lqcd_solve. Profiling (params[i].profile) is not
+ * available here. Returns the most severe status over the lattices. Not in the paper
+ * (its batch is over the rhs of one lattice); nlat: 1..64. */
+lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_params* params,
+                             const int* nrhs, const void* const* b, void* const* x,
+                             lqcd_solve_stats* stats, void* stream);
 
 /* Allocation-free Schur apply. The paper has no counterpart: this entry point
  * exists for callers that cannot let the library allocate device memory while

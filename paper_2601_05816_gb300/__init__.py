@@ -72,6 +72,8 @@ _SIGS = {
     "lqcd_orthogonalise": (_I, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "lqcd_solve": (_I, [_VP, ctypes.POINTER(SolveParams), _I, _VP, _VP, ctypes.POINTER(SolveStats), _VP]),
     "lqcd_tune": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _VP]),
+    "lqcd_solve_batch": (_I, [_I, ctypes.POINTER(_VP), ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(SolveStats), _VP]),
     "lqcd_kernel_variant_count": (_I, [_I]),
     "lqcd_get_kernel_variant": (_I, [_VP, _I, _I, _I]),
     "lqcd_set_kernel_variant": (_I, [_VP, _I, _I, _I, _I]),
@@ -292,3 +294,35 @@ class Lattice:
         return SolveResult(status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                            st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
                            st.kernel_launches, list(its), list(rel))
+
+
+def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
+                max_restarts: int = 200, tol=1e-10, inner_tol: float = 0.0, use_graph: bool = True,
+                reorth: bool = True, stream=None):
+    """Batched GMRES over several lattices of uneven size (lqcd_solve_batch); returns one SolveResult each.
+
+    tol may be one value or one per lattice; b and x complex128 canonical per lattice (host or device).
+    """
+    lib = load()
+    n = len(lattices)
+    tols = list(tol) if isinstance(tol, (list, tuple)) else [tol] * n
+    ctxs = (ctypes.c_void_p * n)(*[lat.handle.value for lat in lattices])
+    params = (SolveParams * n)(*[SolveParams(op, precision, restart_len, max_restarts, tols[i], inner_tol, 0,
+                                             int(use_graph), int(reorth), 0) for i in range(n)])
+    nr = (ctypes.c_int * n)(*[int(v) for v in nrhs])
+    bp = (ctypes.c_void_p * n)(*[_ptr(v) for v in bs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(v) for v in xs])
+    stats = (SolveStats * n)()
+    per_its = [(ctypes.c_int * int(v))() for v in nrhs]
+    per_rel = [(ctypes.c_double * int(v))() for v in nrhs]
+    for i in range(n):
+        stats[i].iters_per_rhs = ctypes.cast(per_its[i], ctypes.POINTER(ctypes.c_int))
+        stats[i].relres_per_rhs = ctypes.cast(per_rel[i], ctypes.POINTER(ctypes.c_double))
+    _check(lib.lqcd_solve_batch(n, ctxs, params, nr, bp, xp, stats, _stream(stream)), "lqcd_solve_batch")
+    out = []
+    for i in range(n):
+        st = stats[i]
+        out.append(SolveResult(st.status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
+                               st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
+                               st.kernel_launches, list(per_its[i]), list(per_rel[i])))
+    return out

@@ -16,14 +16,18 @@ namespace lqcd {
 BlasPlan blas_plan(int64_t n, int nrhs, int num_sms) {
   BlasPlan p;
   p.nrhs = nrhs;
+  p.num_sms = num_sms;
   p.threads = nrhs * (256 / nrhs);
   int64_t want = (n + p.threads - 1) / p.threads;
   int64_t cap = 2 * (int64_t)num_sms;
   p.blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-  // the warp-split Gram-Schmidt kernel needs nrhs <= 32 (one rhs per lane)
-  p.split = nrhs <= 32 ? 1 : 0;
+  // the warp-split Gram-Schmidt kernel: epl = 2 when two elements per lane are possible
+  // (even nrhs <= 64; taken by BF16 storage, and by FP32 above nrhs = 32), else one
+  // (nrhs <= 32)
+  p.epl = (nrhs % 2 == 0 && nrhs <= 64) ? 2 : 1;
+  p.split = (p.epl == 2 || nrhs <= 32) ? 1 : 0;
   if (p.split) {
-    const int64_t rows_per_tile = (32 / nrhs) * 2;
+    const int64_t rows_per_tile = (32 * 2 / nrhs) * 2;   // a lower bound over the kernel shapes
     const int64_t tiles = (n / nrhs + rows_per_tile - 1) / rows_per_tile;
     const int64_t scap = 4 * (int64_t)num_sms;
     p.blocks = (int)(tiles < scap ? (tiles < 1 ? 1 : tiles) : scap);
@@ -179,60 +183,143 @@ gs_pass_kernel(int64_t n, int nrhs, int nvec, const C* __restrict__ basis, int64
   block_reduce_slots<NVB + 1>(vr, vi, nvec + 1, nrhs, partials);
 }
 
-// Warp-split Gram-Schmidt pass (nrhs <= 32). The block vector is viewed as rows of
-// nrhs elements (the packed layout puts the rhs innermost); a warp covers
-// H = 32 / nrhs rows at once, so every lane keeps one rhs. All eight warps of a
-// CTA walk the same element tiles of 32 * U "slots", and warp k owns the basis
-// vectors i = k, k + 8, ...: its loads of those vectors stay in registers. Per
-// tile, the first 32 * U threads ("slot threads", one per tile element) load w;
-// for an update each warp puts its partial sum_i c_i v_i in shared memory and the
-// slot threads form w - sum (one fixed summation order) and store it; the
-// updated tile goes through shared memory to every warp for the dot products.
-// Registers stay low (several CTAs per SM) and each lane keeps NVW * U vector
-// loads in flight.
-template <typename C, typename B, int NVW, int U, bool UPDATE, bool DOTS, bool NORM>
+// Warp-split Gram-Schmidt pass. The block vector is viewed as rows of nrhs
+// elements (the packed layout puts the rhs innermost); each lane owns EPL
+// consecutive elements of a row (EPL = 2: one 16-byte FP32 or 8-byte BF16 load
+// per vector, so every warp load moves 256 B of FP32 / 128-256 B of BF16) and so
+// a fixed set of EPL rhs; a warp covers H = 32 * EPL / nrhs rows at once. All
+// eight warps of a CTA walk the same element tiles of 32 * U "slots" (each slot
+// EPL elements), and warp k owns the basis vectors i = k, k + 8, ...: its loads
+// of those vectors stay in registers, and the loads of the next tile are issued
+// before the current one is processed (register double buffering). For an update
+// each warp puts its partial sum_i c_i v_i in shared memory and the first 32 * U
+// threads ("slot threads", one per slot) form w - sum in one fixed summation
+// order and store it; the updated tile goes through shared memory to every warp
+// for the dot products. Registers stay low (several CTAs per SM).
+// One lane's EPL basis elements as loaded (storage format): the prefetched tile is
+// held in this form, so a BF16 tile in flight costs half the registers of FP32.
+template <typename B, int EPL> struct RawT;
+template <> struct RawT<float2, 1> { using T = float2; };
+template <> struct RawT<float2, 2> { using T = float4; };
+template <> struct RawT<double2, 1> { using T = double2; };
+template <> struct RawT<__nv_bfloat162, 1> { using T = unsigned; };
+template <> struct RawT<__nv_bfloat162, 2> { using T = uint2; };
+
+__device__ __forceinline__ void ld_raw(const float2* p, float2& o) { o = __ldg(p); }
+__device__ __forceinline__ void ld_raw(const float2* p, float4& o) { o = __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void ld_raw(const double2* p, double2& o) { o = __ldg(p); }
+__device__ __forceinline__ void ld_raw(const __nv_bfloat162* p, unsigned& o) {
+  o = __ldg(reinterpret_cast<const unsigned*>(p));
+}
+__device__ __forceinline__ void ld_raw(const __nv_bfloat162* p, uint2& o) {
+  o = __ldg(reinterpret_cast<const uint2*>(p));
+}
+// BF16 -> FP32 is exact: the BF16 bits are the upper half of the FP32 pattern
+__device__ __forceinline__ float2 bf2_to_f2(unsigned u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ void unpack_raw(const float2& r, float2 (&o)[1]) { o[0] = r; }
+__device__ __forceinline__ void unpack_raw(const float4& r, float2 (&o)[2]) {
+  o[0] = make_float2(r.x, r.y);
+  o[1] = make_float2(r.z, r.w);
+}
+__device__ __forceinline__ void unpack_raw(const double2& r, double2 (&o)[1]) { o[0] = r; }
+__device__ __forceinline__ void unpack_raw(const unsigned& r, float2 (&o)[1]) { o[0] = bf2_to_f2(r); }
+__device__ __forceinline__ void unpack_raw(const uint2& r, float2 (&o)[2]) {
+  o[0] = bf2_to_f2(r.x);
+  o[1] = bf2_to_f2(r.y);
+}
+
+// plain (coherent) loads of w, which the same kernel may have written in an earlier pass
+template <int EPL>
+__device__ __forceinline__ void ld_w(const float2* p, float2 (&o)[EPL]) {
+  if constexpr (EPL == 2) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = make_float2(v.x, v.y);
+    o[1] = make_float2(v.z, v.w);
+  } else {
+    o[0] = *p;
+  }
+}
+template <int EPL>
+__device__ __forceinline__ void ld_w(const double2* p, double2 (&o)[EPL]) {
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) o[q] = p[q];
+}
+template <int EPL>
+__device__ __forceinline__ void st_w(float2* p, const float2 (&v)[EPL]) {
+  if constexpr (EPL == 2) *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  else *p = v[0];
+}
+template <int EPL>
+__device__ __forceinline__ void st_w(double2* p, const double2 (&v)[EPL]) {
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) p[q] = v[q];
+}
+template <int EPL>
+__device__ __forceinline__ void st_w(__nv_bfloat162* p, const float2 (&v)[EPL]) {
+  if constexpr (EPL == 2) {
+    const __nv_bfloat162 a = __float22bfloat162_rn(v[0]), b = __float22bfloat162_rn(v[1]);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *reinterpret_cast<uint2*>(p) = u;
+  } else {
+    *p = __float22bfloat162_rn(v[0]);
+  }
+}
+
+template <typename C, typename B, int NVW, int U, int EPL, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(256)
 gs_split_kernel(int64_t n, int nrhs, int nvec, const B* __restrict__ basis, int64_t vstride,
                 C* __restrict__ w, const double2* __restrict__ coef, const double* __restrict__ oscale,
                 B* __restrict__ wout, double2* __restrict__ partials, const int* skip) {
   using Real = typename RealOf<C>::T;
-  static_assert(32 * U <= 256, "one slot thread per tile element");
+  static_assert(32 * U <= 256, "one slot thread per tile slot");
   if (skip != nullptr && *skip != 0) return;
-  __shared__ C part[8][32 * U];
-  __shared__ C wsm[2][32 * U];
-  __shared__ double2 red[8][32];
+  __shared__ C part[8][32 * U * EPL];
+  __shared__ C wsm[2][32 * U * EPL];
+  __shared__ double2 red[8][EPL][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int H = 32 / nrhs;
-  const int r = lane % nrhs;
-  const int hrow = lane / nrhs;
+  const int lanes_per_row = nrhs / EPL;
+  const int H = 32 / lanes_per_row;
+  const int r = (lane % lanes_per_row) * EPL;      // first rhs of this lane
+  const int hrow = lane / lanes_per_row;
   const bool lane_on = hrow < H;
   const int64_t Q = n / nrhs;
   const int64_t tile_rows = (int64_t)H * U;
-  // slot thread: tile element s = threadIdx.x = u * 32 + l, row offset l / nrhs + H u, rhs l % nrhs
+  // slot thread: slot s = threadIdx.x = u * 32 + l, row offset l / lanes_per_row + H u
   const int slot = threadIdx.x;
   const bool is_slot = slot < 32 * U;
   const int s_l = slot & 31, s_u = slot >> 5;
-  const bool s_on = is_slot && (s_l / nrhs) < H;
+  const bool s_on = is_slot && (s_l / lanes_per_row) < H;
+  const int s_r = (s_l % lanes_per_row) * EPL;
   // optional per-rhs factor applied to the updated w before it is stored
-  const Real s_scale = (UPDATE && oscale != nullptr && s_on) ? (Real)oscale[s_l % nrhs] : (Real)1;
-  Real cr[NVW], ci[NVW], ar[NVW], ai[NVW];
+  Real s_scale[EPL];
 #pragma unroll
-  for (int k = 0; k < NVW; ++k) {
-    cr[k] = 0; ci[k] = 0; ar[k] = 0; ai[k] = 0;
-    const int i = warp + 8 * k;
-    if (UPDATE && lane_on && i < nvec) {
-      const double2 c = coef[(int64_t)i * nrhs + r];
-      cr[k] = (Real)c.x;
-      ci[k] = (Real)c.y;
+  for (int q = 0; q < EPL; ++q)
+    s_scale[q] = (UPDATE && oscale != nullptr && s_on) ? (Real)oscale[s_r + q] : (Real)1;
+  Real cr[NVW][EPL], ci[NVW][EPL], ar[NVW][EPL], ai[NVW][EPL];
+#pragma unroll
+  for (int k = 0; k < NVW; ++k)
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) {
+      cr[k][q] = 0; ci[k][q] = 0; ar[k][q] = 0; ai[k][q] = 0;
+      const int i = warp + 8 * k;
+      if (UPDATE && lane_on && i < nvec) {
+        const double2 c = coef[(int64_t)i * nrhs + r + q];
+        cr[k][q] = (Real)c.x;
+        ci[k][q] = (Real)c.y;
+      }
     }
-  }
-  Real nn = 0;
-  // Tile loads: each lane's NVW * U basis elements and, for slot threads, the w element.
-  // The loads of the next tile are issued before the current tile is processed
-  // (register double buffering), so they overlap its barriers and arithmetic.
-  C v[NVW][U], vn[NVW][U];
-  C w_old = C{0, 0}, wn = C{0, 0};
-  auto load_tile = [&](int64_t t, C (&vv)[NVW][U], C& ww) {
+  Real nn[EPL];
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) nn[q] = 0;
+  using R = typename RawT<B, EPL>::T;
+  C v[NVW][U][EPL];
+  R vn[NVW][U];
+  C w_old[EPL], wn[EPL];
+  auto load_tile = [&](int64_t t, R (&vv)[NVW][U], C (&ww)[EPL]) {
     const int64_t row0 = t * tile_rows;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -242,11 +329,17 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const B* __restrict__ basis, int6
 #pragma unroll
       for (int k = 0; k < NVW; ++k) {
         const int i = warp + 8 * k;
-        vv[k][u] = (i < nvec && ok) ? C(ld_basis(basis + i * vstride + e)) : C{0, 0};
+        if (i < nvec && ok) ld_raw(basis + i * vstride + e, vv[k][u]);
+        else vv[k][u] = R{};
       }
     }
-    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
-    ww = (s_on && s_row < Q) ? w[s_row * nrhs + (s_l % nrhs)] : C{0, 0};
+    const int64_t s_row = row0 + s_l / lanes_per_row + (int64_t)H * s_u;
+    if (s_on && s_row < Q) {
+      ld_w<EPL>(w + s_row * nrhs + s_r, ww);
+    } else {
+#pragma unroll
+      for (int q = 0; q < EPL; ++q) ww[q] = C{0, 0};
+    }
   };
   int parity = 0;
   int64_t t = blockIdx.x;
@@ -255,89 +348,108 @@ gs_split_kernel(int64_t n, int nrhs, int nvec, const B* __restrict__ basis, int6
 #pragma unroll
     for (int k = 0; k < NVW; ++k)
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[k][u] = vn[k][u];
-    w_old = wn;
+      for (int u = 0; u < U; ++u) unpack_raw(vn[k][u], v[k][u]);
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) w_old[q] = wn[q];
     if ((t + gridDim.x) * tile_rows < Q) load_tile(t + gridDim.x, vn, wn);
     const int64_t row0 = t * tile_rows;
-    const int64_t s_row = row0 + s_l / nrhs + (int64_t)H * s_u;
+    const int64_t s_row = row0 + s_l / lanes_per_row + (int64_t)H * s_u;
     const bool s_ok = s_on && s_row < Q;
-    const int64_t s_e = s_row * nrhs + (s_l % nrhs);
+    const int64_t s_e = s_row * nrhs + s_r;
     if (UPDATE) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        Real pr = 0, pi = 0;
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int k = 0; k < NVW; ++k) {
-          pr += cr[k] * v[k][u].x - ci[k] * v[k][u].y;
-          pi += cr[k] * v[k][u].y + ci[k] * v[k][u].x;
+        for (int q = 0; q < EPL; ++q) {
+          Real pr = 0, pi = 0;
+#pragma unroll
+          for (int k = 0; k < NVW; ++k) {
+            pr += cr[k][q] * v[k][u][q].x - ci[k][q] * v[k][u][q].y;
+            pi += cr[k][q] * v[k][u][q].y + ci[k][q] * v[k][u][q].x;
+          }
+          part[warp][(u * 32 + lane) * EPL + q] = C{pr, pi};
         }
-        part[warp][u * 32 + lane] = C{pr, pi};
-      }
       __syncthreads();
       if (is_slot) {
-        Real sr = 0, si = 0;
+        C w_new[EPL], ws[EPL];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const C pq = part[q][slot];
-          sr += pq.x;
-          si += pq.y;
+        for (int q = 0; q < EPL; ++q) {
+          Real sr = 0, si = 0;
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const C pq = part[p][slot * EPL + q];
+            sr += pq.x;
+            si += pq.y;
+          }
+          w_new[q] = C{w_old[q].x - sr, w_old[q].y - si};
+          ws[q] = C{w_new[q].x * s_scale[q], w_new[q].y * s_scale[q]};
+          wsm[parity][slot * EPL + q] = w_new[q];
+          if (NORM) nn[q] += w_new[q].x * w_new[q].x + w_new[q].y * w_new[q].y;
         }
-        const C w_new = C{w_old.x - sr, w_old.y - si};
         if (s_ok) {
-          const C ws = C{w_new.x * s_scale, w_new.y * s_scale};
-          if (wout != nullptr) store_as(wout + s_e, ws);  // the normalised vector goes to the basis
-          else w[s_e] = ws;
+          if (wout != nullptr) st_w<EPL>(wout + s_e, ws);  // the normalised vector goes to the basis
+          else st_w<EPL>(w + s_e, ws);
         }
-        wsm[parity][slot] = w_new;
-        if (NORM) nn += w_new.x * w_new.x + w_new.y * w_new.y;
       }
     } else if (is_slot) {
-      wsm[parity][slot] = w_old;
-      if (NORM) nn += w_old.x * w_old.x + w_old.y * w_old.y;
+#pragma unroll
+      for (int q = 0; q < EPL; ++q) {
+        wsm[parity][slot * EPL + q] = w_old[q];
+        if (NORM) nn[q] += w_old[q].x * w_old[q].x + w_old[q].y * w_old[q].y;
+      }
     }
     __syncthreads();
     if (DOTS) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const C wv = wsm[parity][u * 32 + lane];
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int k = 0; k < NVW; ++k) {
-          ar[k] += v[k][u].x * wv.x + v[k][u].y * wv.y;
-          ai[k] += v[k][u].x * wv.y - v[k][u].y * wv.x;
+        for (int q = 0; q < EPL; ++q) {
+          const C wv = wsm[parity][(u * 32 + lane) * EPL + q];
+#pragma unroll
+          for (int k = 0; k < NVW; ++k) {
+            ar[k][q] += v[k][u][q].x * wv.x + v[k][u][q].y * wv.y;
+            ai[k][q] += v[k][u][q].x * wv.y - v[k][u][q].y * wv.x;
+          }
         }
-      }
     }
   }
-  // per-(vector, rhs) sums over the lanes of a warp that share the rhs
+  // per-(vector, rhs) sums over the lanes of a warp that share the rhs: rhs R sits in
+  // element q = R % EPL of the lanes (R / EPL) + h * lanes_per_row, h < H
   const int nslots = nvec + 1;
 #pragma unroll
   for (int k = 0; k < NVW; ++k) {
-    red[warp][lane] = make_double2(DOTS ? (double)ar[k] : 0.0, DOTS ? (double)ai[k] : 0.0);
+#pragma unroll
+    for (int q = 0; q < EPL; ++q)
+      red[warp][q][lane] = make_double2(DOTS ? (double)ar[k][q] : 0.0, DOTS ? (double)ai[k][q] : 0.0);
     __syncwarp();
     const int i = warp + 8 * k;
-    if (lane < nrhs && i < nvec) {
+    // nrhs can exceed 32 with EPL = 2: a lane then writes rhs lane and lane + 32
+    for (int R = lane; R < nrhs && i < nvec; R += 32) {
+      const int q = R % EPL, l0 = R / EPL;
       double2 acc = make_double2(0.0, 0.0);
       for (int h = 0; h < H; ++h) {
-        acc.x += red[warp][lane + h * nrhs].x;
-        acc.y += red[warp][lane + h * nrhs].y;
+        acc.x += red[warp][q][l0 + h * lanes_per_row].x;
+        acc.y += red[warp][q][l0 + h * lanes_per_row].y;
       }
-      partials[((int64_t)blockIdx.x * nslots + i) * nrhs + lane] = acc;
+      partials[((int64_t)blockIdx.x * nslots + i) * nrhs + R] = acc;
     }
     __syncwarp();
   }
-  // the norm is held by the slot threads (warps 0 .. U-1), lane l with rhs l % nrhs
+  // the norm is held by the slot threads (warps 0 .. U-1)
   __syncthreads();
-  red[warp][lane] = make_double2(NORM && is_slot ? (double)nn : 0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) red[warp][q][lane] = make_double2(NORM && is_slot ? (double)nn[q] : 0.0, 0.0);
   __syncthreads();
   if (threadIdx.x < nrhs) {
+    const int q = threadIdx.x % EPL, l0 = threadIdx.x / EPL;
     double acc = 0.0;
     for (int u = 0; u < U; ++u)
-      for (int h = 0; h < H; ++h) acc += red[u][threadIdx.x + h * nrhs].x;
+      for (int h = 0; h < H; ++h) acc += red[u][q][l0 + h * lanes_per_row].x;
     partials[((int64_t)blockIdx.x * nslots + nvec) * nrhs + threadIdx.x] = make_double2(acc, 0.0);
   }
 }
 
-template <typename C, typename B, int NVW, int U>
+template <typename C, typename B, int NVW, int U, int EPL>
 static void gs_split_dispatch(int blocks, int64_t n, int nrhs, int nvec, const void* basis, int64_t vstride,
                               void* w, const void* coef, const double* oscale, void* wout, bool update, bool dots,
                               bool norm, void* partials, const int* skip, cudaStream_t stream) {
@@ -347,7 +459,7 @@ static void gs_split_dispatch(int blocks, int64_t n, int nrhs, int nvec, const v
   const double2* cf = (const double2*)coef;
   double2* pa = (double2*)partials;
 #define GSS_LAUNCH(UP, D, N)                                                                             \
-  gs_split_kernel<C, B, NVW, U, UP, D, N><<<blocks, 256, 0, stream>>>(n, nrhs, nvec, b, vstride, wp, cf, \
+  gs_split_kernel<C, B, NVW, U, EPL, UP, D, N><<<blocks, 256, 0, stream>>>(n, nrhs, nvec, b, vstride, wp, cf, \
                                                                       oscale, wo, pa, skip)
   if (update) {
     if (dots) { if (norm) GSS_LAUNCH(true, true, true); else GSS_LAUNCH(true, true, false); }
@@ -385,13 +497,35 @@ cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, 
                            cudaStream_t stream, const double* oscale, bool basis_bf16, void* wout) {
   if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
   if (basis_bf16 && (f64 || !plan.split)) return cudaErrorInvalidValue;
-  if (plan.split) {
-#define GSS_NVW(NW)                                                                                       \
-  if (f64) gs_split_dispatch<double2, double2, NW, (NW >= 4 ? 1 : 4 / NW)>(plan.blocks, n, plan.nrhs, nvec, \
-      basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);                  \
-  else if (basis_bf16) gs_split_dispatch<float2, __nv_bfloat162, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, \
-      n, plan.nrhs, nvec, basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream); \
-  else gs_split_dispatch<float2, float2, NW, (NW >= 8 ? 1 : 8 / NW)>(plan.blocks, n, plan.nrhs, nvec,       \
+  if (!f64) {
+    int used = 0;
+    const cudaError_t e =
+        basis_bf16 ? launch_gs_stream_bf16(plan, n, nvec, basis, vstride, w, coef, update, dots, norm, partials,
+                                           skip, stream, oscale, wout, &used)
+                   : launch_gs_stream_f32(plan, n, nvec, basis, vstride, w, coef, update, dots, norm, partials,
+                                          skip, stream, oscale, wout, &used);
+    if (e == cudaSuccess) {
+      if (!dots && !norm) return cudaSuccess;
+      return launch_reduce(used, (nvec + 1) * plan.nrhs, partials, out, skip, stream);
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
+  // FP64 runs the split kernel with one element per lane, so only for nrhs <= 32
+  if (plan.split && (!f64 || plan.nrhs <= 32)) {
+  // Elements per lane: FP64 and FP32 take one (a 16- / 8-byte load per lane) up to
+  // nrhs = 32, FP32 two above; BF16 takes two for even nrhs (8-byte loads). Tiles of
+  // U slots keep about 2 KB of basis loads in flight per warp (U * NVW loads).
+#define GSS_NVW(NW)                                                                                        \
+  if (f64) gs_split_dispatch<double2, double2, NW, (NW >= 4 ? 1 : 4 / NW), 1>(plan.blocks, n, plan.nrhs, nvec, \
+      basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);                   \
+  else if (basis_bf16 && plan.epl == 2) gs_split_dispatch<float2, __nv_bfloat162, NW, (NW >= 8 ? 1 : 8 / NW), 2>( \
+      plan.blocks, n, plan.nrhs, nvec, basis, vstride, w, coef, oscale, wout, update, dots, norm, partials,    \
+      skip, stream);                                                                                          \
+  else if (basis_bf16) gs_split_dispatch<float2, __nv_bfloat162, NW, (NW >= 8 ? 1 : 8 / NW), 1>(plan.blocks,  \
+      n, plan.nrhs, nvec, basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);  \
+  else if (plan.nrhs > 32) gs_split_dispatch<float2, float2, NW, (NW >= 4 ? 1 : 4 / NW), 2>(plan.blocks, n,  \
+      plan.nrhs, nvec, basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);   \
+  else gs_split_dispatch<float2, float2, NW, (NW >= 8 ? 1 : 8 / NW), 1>(plan.blocks, n, plan.nrhs, nvec,     \
       basis, vstride, w, coef, oscale, wout, update, dots, norm, partials, skip, stream);
     if (nvec <= 8) { GSS_NVW(1) }
     else if (nvec <= 16) { GSS_NVW(2) }

@@ -60,6 +60,16 @@ lqcd_status workspace(lqcd_ctx ctx, const char* name, size_t bytes, void** out) 
   return LQCD_OK;
 }
 
+// Device word set by the streaming kernels when a pipeline wait gives up (zeroed
+// when first allocated; null if the allocation fails, which disables those kernels).
+int* wait_flag(lqcd_ctx ctx) {
+  const bool fresh = ctx->ws.find("wait_flag") == ctx->ws.end() || ctx->ws["wait_flag"].p == nullptr;
+  void* p = nullptr;
+  if (workspace(ctx, "wait_flag", sizeof(int), &p) != LQCD_OK) return nullptr;
+  if (fresh && cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+  return (int*)p;
+}
+
 lqcd_status pinned_staging(lqcd_ctx ctx, size_t bytes, void** out) {
   if (ctx->pinned_bytes < bytes) {
     if (ctx->pinned) cudaFreeHost(ctx->pinned);

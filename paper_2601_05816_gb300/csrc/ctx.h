@@ -64,6 +64,7 @@ lqcd_status cuda_error(cudaError_t e, const char* what);
 // Grow-only named device workspace.
 lqcd_status workspace(lqcd_ctx ctx, const char* name, size_t bytes, void** out);
 lqcd_status pinned_staging(lqcd_ctx ctx, size_t bytes, void** out);
+int* wait_flag(lqcd_ctx ctx);
 
 int site_tile_log2(const lqcd_ctx_s* ctx, int nrhs);
 PackedLayout layout_for(const lqcd_ctx_s* ctx, int nrhs);

@@ -1,0 +1,423 @@
+// Streaming Gram-Schmidt pass: warp-specialised, basis tiles staged in shared
+// memory by bulk asynchronous copies (cp.async.bulk, completion on mbarriers).
+//
+// The pass is the one of Algorithm 2's orthogonalisation step (classical
+// Gram-Schmidt with one re-orthogonalisation, Sec. III-B-2) on a block of nrhs
+// systems stored rhs-innermost. A tile is a range of whole rows of nrhs
+// elements, so the tile of basis vector i is one contiguous range of memory and
+// one bulk copy per vector (plus one for w) fills a pipeline stage. The bytes in
+// flight are set by the stage count and size, not by registers or occupancy.
+//
+// Warp 8 is the producer: its lane 0 waits until a stage is free, and its lanes
+// issue the copies of the next tile into it (one vector per lane). Warps 0-7 consume: each owns whole rows of a
+// tile (a lane owns EPL consecutive elements of a row, hence a fixed set of
+// rhs) and ALL basis vectors for them, so
+//   w'   = w - sum_i c_i v_i            (update; coefficients staged in shared memory)
+//   a_i += conj(v_i) w'                 (dots, per thread and vector, in registers)
+//   n   += |w'|^2                       (norm)
+// need no exchange between warps: there is no block-wide barrier per tile, a warp
+// releases a stage with one mbarrier arrival. The per-(vector, rhs) sums over
+// lanes and warps, and the norm, go to per-CTA partials in a fixed order at the
+// end (deterministic, like every reduction here).
+#pragma once
+#include "kernels.h"
+
+namespace lqcd {
+namespace gss {
+
+struct Args {
+  int64_t Q;           // rows of nrhs elements (n / nrhs)
+  int64_t vstride;     // elements between basis vectors
+  int nrhs, nvec;
+  int S;               // pipeline stages
+  int TR;              // rows per tile = 8 * H * J, a multiple of 4
+  int J;               // warp steps per consumer warp per tile
+  int lpr, H;          // lanes per row (nrhs / EPL), rows per warp step (32 / lpr)
+  int red_vecs;        // vectors per round of the final reduction
+  uint32_t vt_bytes;   // bytes of one vector's tile in a stage
+  uint32_t stage_bytes;
+  uint32_t coef_off;   // shared-memory offsets (bytes) of the coefficients and the stages
+  uint32_t stage_off;
+  const void* basis;
+  void* w;
+  const double2* coef;
+  const double* oscale;
+  void* wout;
+  double2* partials;
+  const int* skip;
+  int* err;            // set (bit 0) if a pipeline wait gave up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity to complete; gives up after about one
+// second (or 2^28 polls), which never happens unless a copy or an arrival was lost.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < (1u << 28); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && global_ns() - t0 > 1000000000ull) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// shared-memory loads of EPL consecutive basis elements -> FP32 complex
+__device__ __forceinline__ float2 bf16pair(unsigned u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+template <int EPL>
+__device__ __forceinline__ void lds(const float2* p, float2 (&o)[EPL]) {
+  if constexpr (EPL == 2) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = make_float2(v.x, v.y);
+    o[1] = make_float2(v.z, v.w);
+  } else {
+    o[0] = *p;
+  }
+}
+template <int EPL>
+__device__ __forceinline__ void lds(const __nv_bfloat162* p, float2 (&o)[EPL]) {
+  if constexpr (EPL == 2) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    o[0] = bf16pair(u.x);
+    o[1] = bf16pair(u.y);
+  } else {
+    o[0] = bf16pair(*reinterpret_cast<const unsigned*>(p));
+  }
+}
+// global stores of the updated w: FP32 (w itself) or the basis storage type (wout)
+template <int EPL>
+__device__ __forceinline__ void stg(float2* p, const float2 (&v)[EPL]) {
+  if constexpr (EPL == 2) *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  else *p = v[0];
+}
+template <int EPL>
+__device__ __forceinline__ void stg(__nv_bfloat162* p, const float2 (&v)[EPL]) {
+  if constexpr (EPL == 2) {
+    const __nv_bfloat162 a = __float22bfloat162_rn(v[0]), b = __float22bfloat162_rn(v[1]);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *reinterpret_cast<uint2*>(p) = u;
+  } else {
+    *p = __float22bfloat162_rn(v[0]);
+  }
+}
+
+constexpr int kConsumers = 8;                 // consumer warps
+constexpr int kThreads = 32 * (kConsumers + 1);
+
+// Two CTAs per SM while the dot accumulators fit the smaller register share.
+__host__ __device__ constexpr bool two_ctas(int nv, int epl) { return nv * epl <= 16; }
+
+// NV: the largest nvec of the instance (8, 16, 24 or 32): the dot accumulators
+// a_i live in registers, NV * EPL complex per thread.
+template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM>
+__global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream_kernel(const Args a) {
+  using C = float2;
+  if (a.skip != nullptr && *a.skip != 0) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int S = a.S;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  C* cs = reinterpret_cast<C*>(smem + a.coef_off);           // [nvec][nrhs] coefficients, FP32
+  unsigned char* stages = smem + a.stage_off;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nrhs = a.nrhs, nvec = a.nvec, lpr = a.lpr, H = a.H, J = a.J, TR = a.TR;
+  const int hrow = lane / lpr;
+  const bool lane_on = hrow < H;
+  const int r = (lane % lpr) * EPL;  // first rhs of this lane, the same in every row it owns
+  const int64_t Q = a.Q;
+  const int64_t ntiles = (Q + TR - 1) / TR;
+  const int64_t G = gridDim.x;
+  const int L = (int)((ntiles - blockIdx.x + G - 1) / G);  // tiles of this CTA
+  const int vte = (int)(a.vt_bytes / sizeof(B));
+  const B* basis = (const B*)a.basis;
+  C* w = (C*)a.w;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumers);
+    }
+    *abort_flag = 0;
+    fence_proxy_async();  // the initialised barriers are seen by the copy engine
+  }
+  if (UPDATE)
+    for (int t = tid; t < nvec * nrhs; t += kThreads) {
+      const double2 c = a.coef[t];
+      cs[t] = make_float2((float)c.x, (float)c.y);
+    }
+  __syncthreads();
+
+  float ar[NV][EPL], ai[NV][EPL];
+  float nn[EPL], sc[EPL];
+#pragma unroll
+  for (int q = 0; q < EPL; ++q) {
+    nn[q] = 0.f;
+    sc[q] = (UPDATE && a.oscale != nullptr && lane_on && warp < kConsumers) ? (float)a.oscale[r + q] : 1.f;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { ar[i][q] = 0.f; ai[i][q] = 0.f; }
+  }
+
+  if (warp == kConsumers) {
+    // ---------------- producer: lane 0 waits for the stage and posts the byte count,
+    // the lanes issue one copy each (vector i on lane i % 32, w after the vectors)
+    int issued = 0;
+    for (int l = 0; l < L; ++l) {
+      const int s = l % S;
+      const int64_t row0 = (blockIdx.x + (int64_t)l * G) * TR;
+      const int64_t rows = (Q - row0) < TR ? (Q - row0) : TR;
+      const uint32_t vbytes = (uint32_t)(rows * nrhs * (int64_t)sizeof(B));
+      const uint32_t wbytes = (uint32_t)(rows * nrhs * (int64_t)sizeof(C));
+      int go = 1;
+      if (lane == 0) {
+        if (l >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(l / S - 1) & 1u)) {
+          *abort_flag = 1;
+          atomicOr(a.err, 1);
+        }
+        go = *abort_flag ? 0 : 1;
+        if (go) mbar_expect_tx(&full[s], vbytes * (uint32_t)nvec + wbytes);
+      }
+      go = __shfl_sync(0xffffffffu, go, 0);
+      if (!go) break;
+      unsigned char* st = stages + (size_t)s * a.stage_bytes;
+      for (int i = lane; i <= nvec; i += 32) {
+        if (i < nvec) bulk_load(st + (size_t)i * a.vt_bytes, basis + i * a.vstride + row0 * nrhs, vbytes, &full[s]);
+        else bulk_load(st + (size_t)nvec * a.vt_bytes, w + row0 * nrhs, wbytes, &full[s]);
+      }
+      issued = l + 1;
+    }
+    if (lane == 0 && *abort_flag) {
+      // the copies still in flight land before the stages are reused below
+      for (int l = issued - S < 0 ? 0 : issued - S; l < issued; ++l)
+        mbar_wait_bounded(&full[l % S], (uint32_t)(l / S) & 1u);
+    }
+  } else {
+    // ---------------- consumers
+    for (int l = 0; l < L; ++l) {
+      const int s = l % S;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)(l / S) & 1u)) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1);
+        break;
+      }
+      const int64_t row0 = (blockIdx.x + (int64_t)l * G) * TR;
+      const int rows = (int)((Q - row0) < TR ? (Q - row0) : TR);
+      const unsigned char* st = stages + (size_t)s * a.stage_bytes;
+      const B* vt = reinterpret_cast<const B*>(st);
+      const C* wt = reinterpret_cast<const C*>(st + (size_t)nvec * a.vt_bytes);
+      for (int j = 0; j < J; ++j) {
+        const int row = (j * kConsumers + warp) * H + hrow;
+        if (!(lane_on && row < rows)) continue;
+        const int e = row * nrhs + r;
+        C wn[EPL];
+#pragma unroll
+        for (int q = 0; q < EPL; ++q) wn[q] = wt[e + q];
+        if (UPDATE) {
+          // four interleaved partial sums (i mod 4), combined in a fixed order
+          float pr[4][EPL], pi[4][EPL];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < EPL; ++q) { pr[u][q] = 0.f; pi[u][q] = 0.f; }
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            if (i < nvec) {
+              C v[EPL];
+              lds<EPL>(vt + (size_t)i * vte + e, v);
+#pragma unroll
+              for (int q = 0; q < EPL; ++q) {
+                const C c = cs[i * nrhs + r + q];
+                pr[i & 3][q] += c.x * v[q].x - c.y * v[q].y;
+                pi[i & 3][q] += c.x * v[q].y + c.y * v[q].x;
+              }
+            }
+          }
+          C ws[EPL];
+#pragma unroll
+          for (int q = 0; q < EPL; ++q) {
+            const float sr = (pr[0][q] + pr[1][q]) + (pr[2][q] + pr[3][q]);
+            const float si = (pi[0][q] + pi[1][q]) + (pi[2][q] + pi[3][q]);
+            wn[q] = make_float2(wn[q].x - sr, wn[q].y - si);
+            ws[q] = make_float2(wn[q].x * sc[q], wn[q].y * sc[q]);
+          }
+          if (a.wout != nullptr) stg<EPL>((B*)a.wout + row0 * nrhs + e, ws);
+          else stg<EPL>(w + row0 * nrhs + e, ws);
+        }
+        if (NORM) {
+#pragma unroll
+          for (int q = 0; q < EPL; ++q) nn[q] += wn[q].x * wn[q].x + wn[q].y * wn[q].y;
+        }
+        if (DOTS) {
+#pragma unroll
+          for (int i = 0; i < NV; ++i) {
+            if (i < nvec) {
+              C v[EPL];
+              lds<EPL>(vt + (size_t)i * vte + e, v);
+#pragma unroll
+              for (int q = 0; q < EPL; ++q) {
+                ar[i][q] += v[q].x * wn[q].x + v[q].y * wn[q].y;
+                ai[i][q] += v[q].x * wn[q].y - v[q].y * wn[q].x;
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+      if (*abort_flag) break;
+    }
+  }
+
+  // per-(vector, rhs) sums over the H lanes of a warp that share the rhs, then over
+  // the consumer warps, in that fixed order; red_vecs vectors per round
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(stages);  // [red_vecs][8 warps][EPL][32 lanes]; stages idle
+  const int nslots = nvec + 1;
+  const int RV = a.red_vecs;
+  for (int i0 = 0; i0 < nvec; i0 += RV) {
+    if (warp < kConsumers) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i >= i0 && i < i0 + RV && i < nvec)
+#pragma unroll
+          for (int q = 0; q < EPL; ++q)
+            red[(((i - i0) * kConsumers + warp) * EPL + q) * 32 + lane] =
+                make_double2(DOTS ? (double)ar[i][q] : 0.0, DOTS ? (double)ai[i][q] : 0.0);
+    }
+    __syncthreads();
+    for (int t2 = tid; t2 < RV * nrhs; t2 += kThreads) {
+      const int di = t2 / nrhs, R = t2 % nrhs;
+      const int i = i0 + di;
+      if (i < nvec) {
+        const int q = R % EPL, l0 = R / EPL;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int wp = 0; wp < kConsumers; ++wp)
+          for (int h = 0; h < H; ++h) {
+            const double2 v = red[((di * kConsumers + wp) * EPL + q) * 32 + l0 + h * lpr];
+            acc.x += v.x;
+            acc.y += v.y;
+          }
+        a.partials[((int64_t)blockIdx.x * nslots + i) * nrhs + R] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (warp < kConsumers) {
+#pragma unroll
+    for (int q = 0; q < EPL; ++q) red[(warp * EPL + q) * 32 + lane] = make_double2(NORM ? (double)nn[q] : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int R = tid; R < nrhs; R += kThreads) {
+    const int q = R % EPL, l0 = R / EPL;
+    double acc = 0.0;
+    for (int wp = 0; wp < kConsumers; ++wp)
+      for (int h = 0; h < H; ++h) acc += red[(wp * EPL + q) * 32 + l0 + h * lpr].x;
+    a.partials[((int64_t)blockIdx.x * nslots + nvec) * nrhs + R] = make_double2(acc, 0.0);
+  }
+}
+
+// Tile geometry for one pass; ok = false when no stage layout fits shared memory.
+struct Plan {
+  bool ok = false;
+  int J = 1, S = 2, TR = 4, lpr = 1, H = 1, ctas_per_sm = 1, red_vecs = 1;
+  uint32_t vt_bytes = 0, stage_bytes = 0, coef_off = 0, stage_off = 0;
+  size_t smem = 0;
+};
+
+// nv: the instance's vector capacity (8, 16, 24 or 32)
+inline Plan make_plan(int nrhs, int nvec, int nv, int epl, int elem_bytes, bool update) {
+  Plan p;
+  if (nrhs % epl != 0 || nrhs / epl > 32 || nvec < 1 || nvec > nv) return p;
+  p.lpr = nrhs / epl;
+  p.H = 32 / p.lpr;
+  const int unit = kConsumers * p.H;  // rows per unit of J
+  int jstep = 1;
+  while ((unit * jstep) % 4 != 0) ++jstep;
+  const size_t red_one = (size_t)kConsumers * epl * 32 * sizeof(double2);
+  const bool two = two_ctas(nv, epl);
+  const size_t budget = two ? 112 * 1024 : 225 * 1024;
+  p.coef_off = 128;
+  const size_t coef_bytes = update ? ((size_t)nvec * nrhs * sizeof(float2) + 127) / 128 * 128 : 0;
+  p.stage_off = (uint32_t)(128 + coef_bytes);
+  auto stage_of = [&](int J, uint32_t* vt) {
+    const size_t TR = (size_t)unit * J;
+    *vt = (uint32_t)(TR * nrhs * elem_bytes);
+    const size_t stage = (size_t)nvec * *vt + TR * nrhs * sizeof(float2);
+    return (stage + 127) / 128 * 128;
+  };
+  auto fits = [&](int J, int S) {
+    uint32_t vt;
+    const size_t stage = stage_of(J, &vt);
+    const size_t st = (size_t)S * stage > red_one ? (size_t)S * stage : red_one;
+    return p.stage_off + st <= budget;
+  };
+  // up to 4 (two CTAs per SM) or 6 stages; the largest tile with a stage of at most
+  // 32 KB, else the smallest tile (8 warps x H rows) if it fits
+  for (int S = two ? 4 : 6; S >= 2; --S) {
+    int best = 0;
+    for (int J = jstep; J <= 64; J += jstep) {
+      uint32_t vt;
+      if (fits(J, S) && stage_of(J, &vt) <= 32 * 1024) best = J;
+    }
+    if (best == 0 && fits(jstep, S)) best = jstep;
+    if (best > 0) {
+      p.J = best;
+      p.S = S;
+      p.TR = unit * best;
+      p.stage_bytes = (uint32_t)stage_of(best, &p.vt_bytes);
+      const size_t st = (size_t)S * p.stage_bytes > red_one ? (size_t)S * p.stage_bytes : red_one;
+      p.smem = p.stage_off + st;
+      p.red_vecs = (int)(st / red_one);
+      if (p.red_vecs > nvec) p.red_vecs = nvec;
+      if (p.red_vecs < 1) p.red_vecs = 1;
+      p.ctas_per_sm = two ? 2 : 1;
+      p.ok = true;
+      return p;
+    }
+  }
+  return p;
+}
+
+}  // namespace gss
+}  // namespace lqcd

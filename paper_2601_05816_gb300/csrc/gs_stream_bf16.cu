@@ -1,0 +1,12 @@
+// Streaming Gram-Schmidt pass, BF16 basis (FP32 arithmetic, FP32 w).
+#include "gs_stream_impl.cuh"
+
+namespace lqcd {
+cudaError_t launch_gs_stream_bf16(const BlasPlan& plan, int64_t n, int nvec, const void* basis,
+                                  int64_t vstride, void* w, const void* coef, bool update, bool dots, bool norm,
+                                  void* partials, const int* skip, cudaStream_t stream, const double* oscale,
+                                  void* wout, int* blocks_used) {
+  return gss::launch_stream<__nv_bfloat162>(plan, n, nvec, basis, vstride, w, coef, update, dots, norm, partials,
+                                            skip, stream, oscale, wout, blocks_used);
+}
+}  // namespace lqcd

@@ -29,9 +29,27 @@ struct BlasPlan {
   int nrhs;
   int threads;   // multiple of nrhs, <= 256
   int blocks;    // CTAs of the streaming kernels
-  int split;     // 1: Gram-Schmidt passes use the warp-split kernel (nrhs <= 32)
+  int split;     // 1: Gram-Schmidt passes use the warp-split kernel
+  int epl;       // 2: the warp-split kernel may put two elements (rhs) per lane (even nrhs <= 64)
+  int num_sms;
+  // device word that the streaming Gram-Schmidt kernel sets when a pipeline wait gives
+  // up (never in correct operation); null: the streaming kernel is not used
+  int* wait_flag = nullptr;
 };
 BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
+
+// gs_stream_*.cu: the Gram-Schmidt pass with basis tiles staged in shared memory by
+// bulk asynchronous copies (FP32 or BF16 basis, nrhs <= 32 or even nrhs <= 64).
+// Returns cudaErrorNotSupported (launching nothing) when no layout fits; on success
+// the per-CTA partials of *blocks_used CTAs are written.
+cudaError_t launch_gs_stream_f32(const BlasPlan& plan, int64_t n, int nvec, const void* basis, int64_t vstride,
+                                 void* w, const void* coef, bool update, bool dots, bool norm, void* partials,
+                                 const int* skip, cudaStream_t stream, const double* oscale, void* wout,
+                                 int* blocks_used);
+cudaError_t launch_gs_stream_bf16(const BlasPlan& plan, int64_t n, int nvec, const void* basis,
+                                  int64_t vstride, void* w, const void* coef, bool update, bool dots, bool norm,
+                                  void* partials, const int* skip, cudaStream_t stream, const double* oscale,
+                                  void* wout, int* blocks_used);
 
 // Fused block Gram-Schmidt pass over nvec basis vectors v_i = basis + i * vstride:
 //   if update: w <- w - sum_i coef[i][r] v_i   (coef: device double2 [nvec][nrhs])

@@ -366,7 +366,8 @@ static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n,
 
 }  // namespace lqcd
 
-using namespace lqcd;
+
+namespace lqcd {
 
 // Pinned staging layout used by the solve (host side of the per-rhs scalars).
 struct Staging {
@@ -375,82 +376,84 @@ struct Staging {
   double thr[256];
   int active[256];
   int kcycle[256];
+  int wait_err;             // the streaming kernels' pipeline-wait flag
 };
 
-extern "C" {
+// One lattice's batched-GMRES solve, split into the phases of a restart so that
+// a single solve and a batch of solves on several lattices share the same code.
+struct SolveJob {
+  lqcd_ctx ctx = nullptr;
+  lqcd_solve_params P;
+  int nrhs = 0;
+  const void* b = nullptr;
+  void* x = nullptr;
+  lqcd_solve_stats* stats = nullptr;
+  cudaStream_t s = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  bool eo = false, f64_inner = false, bf16 = false, reorth = true;
+  int m = 0;
+  double inner_tol = 0.0;
+  int64_t n_full = 0, n_half = 0, n_sys = 0;
+  size_t full64 = 0;
+  void *b_can = nullptr, *x_can = nullptr, *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+  void *bhat = nullptr, *tmp64 = nullptr, *sys_b = nullptr, *sys_x = nullptr, *red_partials = nullptr;
+  bool b_host = false, x_host = false;
+  SolveBufs B;
+  BlasPlan plan_full;
+  double* d_beta0 = nullptr;
+  Staging* hs = nullptr;
+  Profile prof;
+  std::vector<int> iters;
+  std::vector<double> relres, bnorm;
+  int restarts = 0;
+  bool pending_k = false;
+  bool finished = false;
+  long long nl = 0;  // kernel launches of this solve
+  double op_bytes_inner = 0.0;
+  lqcd_status result = LQCD_NOT_CONVERGED;
 
-lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs, int nvec,
-                               const void* basis, void* w, void* h, void* hnorm, int reorth, void* stream) {
-  if (!ctx) return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: null context");
-  if ((dtype != LQCD_C64 && dtype != LQCD_C128 && dtype != LQCD_BF16S) || nrhs < 1 || nrhs > 256 || nvec < 1 ||
-      nvec > 64 || !basis || !w || !h || !hnorm ||
-      (sites != LQCD_SITES_FULL && sites != LQCD_SITES_EVEN && sites != LQCD_SITES_ODD) ||
-      (dtype == LQCD_BF16S && nrhs > 32))
-    return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: bad arguments");
-  cudaStream_t s = (cudaStream_t)stream;
-  const bool f64 = dtype == LQCD_C128;
-  const bool bf16 = dtype == LQCD_BF16S;
-  const int64_t n = (int64_t)packed_elems(ctx, sites, nrhs);
-  BlasPlan plan = blas_plan(n, nrhs, ctx->num_sms);
-  void *partials, *h1, *h2, *hn;
-  const size_t hb = sizeof(double2) * (size_t)(nvec + 1) * nrhs;
-  lqcd_status st = workspace(ctx, "ortho_partials", hb * plan.blocks, &partials);
-  if (st == LQCD_OK) st = workspace(ctx, "ortho_h1", hb, &h1);
-  if (st == LQCD_OK) st = workspace(ctx, "ortho_h2", hb, &h2);
-  if (st == LQCD_OK) st = workspace(ctx, "ortho_hn", hb, &hn);
-  if (st != LQCD_OK) return st;
-  LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, nullptr, false, true, false, partials, h1, nullptr, s,
-                           nullptr, bf16),
-            "gs dots");
-  if (reorth) {
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, true, false, partials, h2, nullptr, s,
-                             nullptr, bf16),
-              "gs update+dots");
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h2, true, false, true, partials, hn, nullptr, s,
-                             nullptr, bf16),
-              "gs update+norm");
-  } else {
-    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, false, true, partials, hn, nullptr, s,
-                             nullptr, bf16),
-              "gs update+norm");
-  }
-  const int q = nvec * nrhs > nrhs ? nvec * nrhs : nrhs;
-  combine_h_kernel<<<(q + 127) / 128, 128, 0, s>>>(nvec, nrhs, (const double2*)h1,
-                                                   reorth ? (const double2*)h2 : nullptr, (const double2*)hn,
-                                                   (double2*)h, (double*)hnorm);
-  LQCD_CUDA(cudaGetLastError(), "combine h");
-  return LQCD_OK;
-}
+  lqcd_status setup(lqcd_ctx c, const lqcd_solve_params* params, int nr, const void* bb, void* xx,
+                    lqcd_solve_stats* st_out, cudaStream_t stream);
+  lqcd_status enqueue_residual();
+  lqcd_status decide(bool* run);   // after the stream has been synchronised
+  lqcd_status enqueue_cycle(cudaStream_t cs, bool allow_graph);
+  lqcd_status finish();
+  // kernels of one restart cycle: cycle_init, v0, per step (operator, Gram-Schmidt
+  // passes with their reductions, givens, normalisation), backsub, update
+  long long cycle_launches() const { return 4 + (long long)m * ((eo ? 2 : 1) + 6); }
+};
 
-lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const void* b, void* x,
-                       lqcd_solve_stats* stats, void* stream) {
-  const auto t0 = std::chrono::steady_clock::now();
-  if (!ctx || !P || !b || !x) return set_error(LQCD_ERR_ARG, "lqcd_solve: null argument");
+lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr, const void* bb, void* xx,
+                            lqcd_solve_stats* st_out, cudaStream_t stream) {
+  t0 = std::chrono::steady_clock::now();
+  ctx = c; nrhs = nr; b = bb; x = xx; stats = st_out; s = stream;
+  if (!ctx || !params || !b || !x) return set_error(LQCD_ERR_ARG, "lqcd_solve: null argument");
+  P = *params;
   if (!ctx->have_gauge || !ctx->have_blocks)
     return set_error(LQCD_ERR_STATE, "lqcd_solve: set_gauge and set_clover must be called first");
-  if (nrhs < 1 || nrhs > 64 || P->restart_len < 1 || P->restart_len > 64 || P->max_restarts < 1 ||
-      !(P->tol > 0.0) || (P->op != LQCD_OP_FULL && P->op != LQCD_OP_SCHUR) ||
-      (P->precision != LQCD_C64 && P->precision != LQCD_C128 && P->precision != LQCD_BF16S) ||
-      (P->precision == LQCD_BF16S && nrhs > 32))
+  if (nrhs < 1 || nrhs > 64 || P.restart_len < 1 || P.restart_len > 64 || P.max_restarts < 1 ||
+      !(P.tol > 0.0) || (P.op != LQCD_OP_FULL && P.op != LQCD_OP_SCHUR) ||
+      (P.precision != LQCD_C64 && P.precision != LQCD_C128 && P.precision != LQCD_BF16S) ||
+      (P.precision == LQCD_BF16S && nrhs > 32 && (nrhs % 2 != 0 || nrhs > 64)))
     return set_error(LQCD_ERR_ARG,
                      "lqcd_solve: bad parameters (nrhs 1..64, 1..32 for BF16 storage, restart_len 1..64, tol > 0)");
-  cudaStream_t s = (cudaStream_t)stream;
-  const bool eo = P->op == LQCD_OP_SCHUR;
-  const bool f64_inner = P->precision == LQCD_C128;
-  const bool bf16 = P->precision == LQCD_BF16S;
-  const int m = P->restart_len;
-  const bool reorth = P->reorth != 0 || bf16;
-  const double inner_tol = P->inner_tol > 0.0 ? P->inner_tol : (f64_inner ? 0.0 : 1e-5);
-  long long nl = 0;  // kernel launches of this call
-  const int64_t n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
-  const int64_t n_half = n_full / 2;
-  const int64_t n_sys = eo ? n_half : n_full;
-  const size_t full64 = (size_t)n_full * sizeof(double2);
+  eo = P.op == LQCD_OP_SCHUR;
+  f64_inner = P.precision == LQCD_C128;
+  bf16 = P.precision == LQCD_BF16S;
+  m = P.restart_len;
+  reorth = P.reorth != 0 || bf16;
+  inner_tol = P.inner_tol > 0.0 ? P.inner_tol : (f64_inner ? 0.0 : 1e-5);
+  n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
+  n_half = n_full / 2;
+  n_sys = eo ? n_half : n_full;
+  full64 = (size_t)n_full * sizeof(double2);
   lqcd_status st;
 
   // ---------------- buffers
-  void *b_can = (void*)b, *x_can = x, *b64, *x64, *r64, *t64, *bhat = nullptr, *tmp64 = nullptr;
-  const bool b_host = !is_device_pointer(b), x_host = !is_device_pointer(x);
+  b_can = (void*)b;
+  x_can = x;
+  b_host = !is_device_pointer(b);
+  x_host = !is_device_pointer(x);
   if (b_host && (st = workspace(ctx, "solve_b_can", full64, &b_can)) != LQCD_OK) return st;
   if (x_host && (st = workspace(ctx, "solve_x_can", full64, &x_can)) != LQCD_OK) return st;
   if ((st = workspace(ctx, "solve_b64", full64, &b64)) != LQCD_OK) return st;
@@ -461,7 +464,6 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     if ((st = workspace(ctx, "solve_bhat", (size_t)n_half * sizeof(double2), &bhat)) != LQCD_OK) return st;
     if ((st = workspace(ctx, "schur_tmp64", (size_t)n_half * sizeof(double2), &tmp64)) != LQCD_OK) return st;
   }
-  SolveBufs B;
   B.f64_inner = f64_inner;
   B.bf16 = bf16;
   B.w32 = nullptr;
@@ -478,6 +480,7 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
       return st;
   }
   B.plan = blas_plan(n_sys, nrhs, ctx->num_sms);
+  B.plan.wait_flag = wait_flag(ctx);
   const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
   if ((st = workspace(ctx, "solve_partials", hb * B.plan.blocks, &B.partials)) != LQCD_OK) return st;
   if ((st = workspace(ctx, "solve_h1", hb, &B.h1)) != LQCD_OK) return st;
@@ -511,13 +514,9 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     B.st.all_done = (int*)take();
     B.st.kmax = (int*)take();
   }
-  double* d_beta0;
   if ((st = workspace(ctx, "solve_beta0", sizeof(double) * nrhs, (void**)&d_beta0)) != LQCD_OK) return st;
-  Staging* hs;
   if ((st = pinned_staging(ctx, sizeof(Staging), (void**)&hs)) != LQCD_OK) return st;
-
-  Profile prof;
-  prof.on = P->profile != 0;
+  prof.on = P.profile != 0;
   if (prof.on) {
     if (ctx->prof_events.empty()) {
       ctx->prof_events.resize(4 * 64);
@@ -529,97 +528,123 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
   // ---------------- inputs
   if (b_host) LQCD_CUDA(cudaMemcpyAsync(b_can, b, full64, cudaMemcpyHostToDevice, s), "upload b");
   if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, b_can, b64, s)) != LQCD_OK) return st;
-  if (P->x0_given) {
+  if (P.x0_given) {
     if (x_host) LQCD_CUDA(cudaMemcpyAsync(x_can, x, full64, cudaMemcpyHostToDevice, s), "upload x0");
     if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x_can, x64, s)) != LQCD_OK) return st;
   } else {
     LQCD_CUDA(cudaMemsetAsync(x64, 0, full64, s), "zero x");
   }
-  BlasPlan plan_full = blas_plan(n_full, nrhs, ctx->num_sms);
-  void* red_partials;
+  plan_full = blas_plan(n_full, nrhs, ctx->num_sms);
   if ((st = workspace(ctx, "solve_partials_full", sizeof(double2) * (size_t)nrhs * plan_full.blocks,
                       &red_partials)) != LQCD_OK)
     return st;
   LQCD_CUDA(launch_norm2(true, plan_full, n_full, b64, red_partials, B.hn, s), "norm b");
-  nl += (P->x0_given ? 2 : 1) + 2 + (eo ? 2 : 0);  // packs, norm + reduction, prepare
+  nl += (P.x0_given ? 2 : 1) + 2 + (eo ? 2 : 0);  // packs, norm + reduction, prepare
   LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read norm b");
   LQCD_CUDA(cudaStreamSynchronize(s), "sync");
-  std::vector<double> bnorm(nrhs);
+  bnorm.assign(nrhs, 0.0);
   for (int r = 0; r < nrhs; ++r) {
     bnorm[r] = std::sqrt(hs->rn2[2 * r]);
     if (!std::isfinite(bnorm[r]))
       return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: right-hand side %d is not finite", r);
   }
-  void* sys_b = b64;
-  void* sys_x = x64;
+  sys_b = b64;
+  sys_x = x64;
   if (eo) {
     if ((st = schur_prepare(ctx, true, nrhs, b64, bhat, tmp64, s)) != LQCD_OK) return st;
     sys_b = bhat;
     sys_x = (char*)x64 + (size_t)n_half * sizeof(double2);
   }
+  iters.assign(nrhs, 0);
+  relres.assign(nrhs, 0.0);
+  op_bytes_inner = op_algorithmic_bytes(ctx, P.op, f64_inner, nrhs, bf16);
+  return LQCD_OK;
+}
 
-  // ---------------- restarts
-  std::vector<int> iters(nrhs, 0);
-  std::vector<double> relres(nrhs, 0.0);
-  const double op_bytes_inner = op_algorithmic_bytes(ctx, P->op, f64_inner, nrhs, bf16);
-  int restarts = 0;
-  lqcd_status result = LQCD_NOT_CONVERGED;
-  bool pending_k = false;
-  for (;;) {
-    // true residual r = b - D x in FP64
-    if ((st = apply_operator(ctx, P->op, true, nrhs, sys_x, t64, tmp64, nullptr, s)) != LQCD_OK) return st;
-    LQCD_CUDA(launch_sub_norm(B.plan, n_sys, sys_b, t64, r64, B.partials, B.hn, s), "residual");
-    LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read rn");
-    LQCD_CUDA(cudaStreamSynchronize(s), "sync residual");
-    nl += eo ? 4 : 3;  // FP64 operator + residual kernel + reduction
-    if (pending_k) {
-      int kmax = 0;
-      for (int r = 0; r < nrhs; ++r) {
-        iters[r] += hs->kcycle[r];
-        kmax = std::max(kmax, hs->kcycle[r]);
-      }
-      collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth, bf16);
-    }
-    pending_k = false;
-    int n_active = 0;
+// True residual r = b - D x in FP64 and its norms copied to the pinned staging area.
+lqcd_status SolveJob::enqueue_residual() {
+  lqcd_status st;
+  if ((st = apply_operator(ctx, P.op, true, nrhs, sys_x, t64, tmp64, nullptr, s)) != LQCD_OK) return st;
+  LQCD_CUDA(launch_sub_norm(B.plan, n_sys, sys_b, t64, r64, B.partials, B.hn, s), "residual");
+  LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read rn");
+  hs->wait_err = 0;
+  if (B.plan.wait_flag)
+    LQCD_CUDA(cudaMemcpyAsync(&hs->wait_err, B.plan.wait_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
+  nl += eo ? 4 : 3;  // FP64 operator + residual kernel + reduction
+  return LQCD_OK;
+}
+
+// Host decision of one restart (the residual norms have arrived): retire the rhs
+// that meet tol, set the cycle thresholds and starting norms, upload them.
+lqcd_status SolveJob::decide(bool* run) {
+  *run = false;
+  if (pending_k) {
+    int kmax = 0;
     for (int r = 0; r < nrhs; ++r) {
-      const double rn = std::sqrt(hs->rn2[2 * r]);
-      if (!std::isfinite(rn))
-        return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: residual of rhs %d is not finite", r);
-      relres[r] = bnorm[r] > 0.0 ? rn / bnorm[r] : 0.0;
-      const bool act = bnorm[r] > 0.0 && rn > P->tol * bnorm[r];
-      hs->active[r] = act ? 1 : 0;
-      hs->beta0[r] = act ? rn : 1.0;
-      // cycle target: half the tolerance (so the true residual, which the Arnoldi
-      // estimate approximates, lands below tol), or the inner relative reduction
-      double thr = 0.5 * P->tol * bnorm[r];
-      if (inner_tol > 0.0) thr = std::max(thr, inner_tol * rn);
-      hs->thr[r] = thr;
-      n_active += act;
+      iters[r] += hs->kcycle[r];
+      kmax = std::max(kmax, hs->kcycle[r]);
     }
-    if (n_active == 0) {
-      result = LQCD_OK;
-      break;
-    }
-    if (restarts >= P->max_restarts) break;
-    LQCD_CUDA(cudaMemcpyAsync(B.st.active, hs->active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s), "up");
-    LQCD_CUDA(cudaMemcpyAsync(B.st.thr, hs->thr, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
-    LQCD_CUDA(cudaMemcpyAsync(d_beta0, hs->beta0, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
-    LQCD_CUDA(launch_cycle_init(B.st, d_beta0, s), "cycle init");
-    LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, s, bf16), "v0");
-    if ((st = run_cycle(ctx, B, P->op, reorth, P->use_graph != 0, &prof, s)) != LQCD_OK) return st;
-    LQCD_CUDA(launch_backsub(B.st, s), "backsub");
-    LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, s, bf16),
-              "update x");
-    // cycle_init, v0, per step (operator, Gram-Schmidt passes with their reductions, givens,
-    // normalisation), backsub, update
-    nl += 4 + (long long)m * ((eo ? 2 : 1) + 6);
-    LQCD_CUDA(cudaMemcpyAsync(hs->kcycle, B.st.k, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s), "read k");
-    pending_k = true;
-    ++restarts;
+    collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth, bf16);
   }
+  pending_k = false;
+  if (hs->wait_err != 0)
+    return set_error(LQCD_ERR_CUDA, "lqcd_solve: a Gram-Schmidt pipeline wait timed out (device flag %d)",
+                     hs->wait_err);
+  int n_active = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const double rn = std::sqrt(hs->rn2[2 * r]);
+    if (!std::isfinite(rn))
+      return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: residual of rhs %d is not finite", r);
+    relres[r] = bnorm[r] > 0.0 ? rn / bnorm[r] : 0.0;
+    const bool act = bnorm[r] > 0.0 && rn > P.tol * bnorm[r];
+    hs->active[r] = act ? 1 : 0;
+    hs->beta0[r] = act ? rn : 1.0;
+    // cycle target: half the tolerance (so the true residual, which the Arnoldi
+    // estimate approximates, lands below tol), or the inner relative reduction
+    double thr = 0.5 * P.tol * bnorm[r];
+    if (inner_tol > 0.0) thr = std::max(thr, inner_tol * rn);
+    hs->thr[r] = thr;
+    n_active += act;
+  }
+  if (n_active == 0) {
+    result = LQCD_OK;
+    finished = true;
+    return LQCD_OK;
+  }
+  if (restarts >= P.max_restarts) {
+    finished = true;
+    return LQCD_OK;
+  }
+  LQCD_CUDA(cudaMemcpyAsync(B.st.active, hs->active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s), "up");
+  LQCD_CUDA(cudaMemcpyAsync(B.st.thr, hs->thr, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
+  LQCD_CUDA(cudaMemcpyAsync(d_beta0, hs->beta0, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
+  *run = true;
+  return LQCD_OK;
+}
 
-  // ---------------- finish: reconstruct, final full-operator residual, output
+// One restart cycle on stream cs: v_0, m Arnoldi steps, back substitution, x += V y.
+lqcd_status SolveJob::enqueue_cycle(cudaStream_t cs, bool allow_graph) {
+  lqcd_status st;
+  LQCD_CUDA(launch_cycle_init(B.st, d_beta0, cs), "cycle init");
+  LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, cs, bf16), "v0");
+  if (allow_graph) {
+    if ((st = run_cycle(ctx, B, P.op, reorth, P.use_graph != 0, &prof, cs)) != LQCD_OK) return st;
+  } else {
+    if ((st = run_cycle_direct(ctx, B, P.op, reorth, &prof, cs)) != LQCD_OK) return st;
+  }
+  LQCD_CUDA(launch_backsub(B.st, cs), "backsub");
+  LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, cs, bf16),
+            "update x");
+  nl += cycle_launches();
+  LQCD_CUDA(cudaMemcpyAsync(hs->kcycle, B.st.k, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, cs), "read k");
+  pending_k = true;
+  ++restarts;
+  return LQCD_OK;
+}
+
+// Reconstruct x_e (odd-even), final full-operator residual, unpack and download x, stats.
+lqcd_status SolveJob::finish() {
+  lqcd_status st;
   if (eo && (st = schur_reconstruct(ctx, true, nrhs, b64, sys_x, x64, s)) != LQCD_OK) return st;
   if ((st = apply_operator(ctx, LQCD_OP_FULL, true, nrhs, x64, t64, nullptr, nullptr, s)) != LQCD_OK) return st;
   LQCD_CUDA(launch_sub_norm(plan_full, n_full, b64, t64, r64, red_partials, B.hn, s), "final residual");
@@ -654,6 +679,176 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
   if (result == LQCD_NOT_CONVERGED)
     set_error(LQCD_NOT_CONVERGED, "lqcd_solve: max_restarts reached, max relative residual %.3e", relmax);
   return result;
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+
+extern "C" {
+
+lqcd_status lqcd_orthogonalise(lqcd_ctx ctx, lqcd_dtype dtype, lqcd_sites sites, int nrhs, int nvec,
+                               const void* basis, void* w, void* h, void* hnorm, int reorth, void* stream) {
+  if (!ctx) return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: null context");
+  if ((dtype != LQCD_C64 && dtype != LQCD_C128 && dtype != LQCD_BF16S) || nrhs < 1 || nrhs > 256 || nvec < 1 ||
+      nvec > 64 || !basis || !w || !h || !hnorm ||
+      (sites != LQCD_SITES_FULL && sites != LQCD_SITES_EVEN && sites != LQCD_SITES_ODD) ||
+      (dtype == LQCD_BF16S && nrhs > 32 && (nrhs % 2 != 0 || nrhs > 64)))
+    return set_error(LQCD_ERR_ARG, "lqcd_orthogonalise: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = dtype == LQCD_C128;
+  const bool bf16 = dtype == LQCD_BF16S;
+  const int64_t n = (int64_t)packed_elems(ctx, sites, nrhs);
+  BlasPlan plan = blas_plan(n, nrhs, ctx->num_sms);
+  plan.wait_flag = wait_flag(ctx);
+  void *partials, *h1, *h2, *hn;
+  const size_t hb = sizeof(double2) * (size_t)(nvec + 1) * nrhs;
+  lqcd_status st = workspace(ctx, "ortho_partials", hb * plan.blocks, &partials);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_h1", hb, &h1);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_h2", hb, &h2);
+  if (st == LQCD_OK) st = workspace(ctx, "ortho_hn", hb, &hn);
+  if (st != LQCD_OK) return st;
+  LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, nullptr, false, true, false, partials, h1, nullptr, s,
+                           nullptr, bf16),
+            "gs dots");
+  if (reorth) {
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, true, false, partials, h2, nullptr, s,
+                             nullptr, bf16),
+              "gs update+dots");
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h2, true, false, true, partials, hn, nullptr, s,
+                             nullptr, bf16),
+              "gs update+norm");
+  } else {
+    LQCD_CUDA(launch_gs_pass(f64, plan, n, nvec, basis, n, w, h1, true, false, true, partials, hn, nullptr, s,
+                             nullptr, bf16),
+              "gs update+norm");
+  }
+  const int q = nvec * nrhs > nrhs ? nvec * nrhs : nrhs;
+  combine_h_kernel<<<(q + 127) / 128, 128, 0, s>>>(nvec, nrhs, (const double2*)h1,
+                                                   reorth ? (const double2*)h2 : nullptr, (const double2*)hn,
+                                                   (double2*)h, (double*)hnorm);
+  LQCD_CUDA(cudaGetLastError(), "combine h");
+  return LQCD_OK;
+}
+
+lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const void* b, void* x,
+                       lqcd_solve_stats* stats, void* stream) {
+  SolveJob job;
+  cudaStream_t s = (cudaStream_t)stream;
+  lqcd_status st = job.setup(ctx, P, nrhs, b, x, stats, s);
+  if (st != LQCD_OK) return st;
+  for (;;) {
+    if ((st = job.enqueue_residual()) != LQCD_OK) return st;
+    LQCD_CUDA(cudaStreamSynchronize(s), "sync residual");
+    bool run = false;
+    if ((st = job.decide(&run)) != LQCD_OK) return st;
+    if (!run) break;
+    if ((st = job.enqueue_cycle(s, true)) != LQCD_OK) return st;
+  }
+  return job.finish();
+}
+
+lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_params* params, const int* nrhs,
+                             const void* const* b, void* const* x, lqcd_solve_stats* stats, void* stream) {
+  if (nlat < 1 || nlat > 64 || !ctxs || !params || !nrhs || !b || !x)
+    return set_error(LQCD_ERR_ARG, "lqcd_solve_batch: bad arguments");
+  for (int i = 0; i < nlat; ++i)
+    for (int k = 0; k < i; ++k)
+      if (ctxs[i] == ctxs[k]) return set_error(LQCD_ERR_ARG, "lqcd_solve_batch: lattice %d appears twice", i);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<SolveJob> jobs(nlat);
+  lqcd_status st;
+  for (int i = 0; i < nlat; ++i) {
+    lqcd_solve_params pi = params[i];
+    pi.profile = 0;   // CUDA events do not time kernels inside a graph
+    if ((st = jobs[i].setup(ctxs[i], &pi, nrhs[i], b[i], x[i], stats ? &stats[i] : nullptr, s)) != LQCD_OK)
+      return st;
+  }
+  // Per lattice a side stream; each restart round's cycles of every lattice still
+  // running are captured once into one graph (fork/join over the side streams, so
+  // the lattices' kernels run concurrently) and replayed as one launch per round.
+  lqcd_ctx c0 = ctxs[0];
+  if (!c0->capture_stream)
+    LQCD_CUDA(cudaStreamCreateWithFlags(&c0->capture_stream, cudaStreamNonBlocking), "capture stream");
+  std::vector<cudaStream_t> side(nlat, nullptr);
+  std::vector<cudaEvent_t> ev(nlat + 1, nullptr);
+  struct Cleanup {
+    std::vector<cudaStream_t>* side;
+    std::vector<cudaEvent_t>* ev;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    ~Cleanup() {
+      if (ex) cudaGraphExecDestroy(ex);
+      if (g) cudaGraphDestroy(g);
+      for (auto h : *side) if (h) cudaStreamDestroy(h);
+      for (auto e : *ev) if (e) cudaEventDestroy(e);
+    }
+  } cleanup{&side, &ev};
+  for (int i = 0; i < nlat; ++i) LQCD_CUDA(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking), "stream");
+  for (auto& e : ev) LQCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+  std::vector<char> running(nlat, 0);
+  std::string graph_key;
+  int rounds = 0;
+  for (;;) {
+    int n_run = 0;
+    for (auto& j : jobs)
+      if (!j.finished && (st = j.enqueue_residual()) != LQCD_OK) return st;
+    LQCD_CUDA(cudaStreamSynchronize(s), "sync residuals");
+    std::string key;
+    for (int i = 0; i < nlat; ++i) {
+      bool run = false;
+      if (!jobs[i].finished && (st = jobs[i].decide(&run)) != LQCD_OK) return st;
+      running[i] = run ? 1 : 0;
+      n_run += run;
+      key += run ? '1' : '0';
+    }
+    if (n_run == 0) break;
+    if (key != graph_key) {   // the set of running lattices changed: capture the round anew
+      if (cleanup.ex) { cudaGraphExecDestroy(cleanup.ex); cleanup.ex = nullptr; }
+      if (cleanup.g) { cudaGraphDestroy(cleanup.g); cleanup.g = nullptr; }
+      cudaStream_t cs = c0->capture_stream;
+      LQCD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+      lqcd_status cst = LQCD_OK;
+      cudaError_t ce = cudaEventRecord(ev[nlat], cs);
+      for (int i = 0; i < nlat && cst == LQCD_OK && ce == cudaSuccess; ++i) {
+        if (!running[i]) continue;
+        ce = cudaStreamWaitEvent(side[i], ev[nlat], 0);
+        if (ce != cudaSuccess) break;
+        const int restarts_before = jobs[i].restarts;
+        cst = jobs[i].enqueue_cycle(side[i], false);
+        jobs[i].restarts = restarts_before;   // restarts and launches are counted per replay below
+        jobs[i].nl -= jobs[i].cycle_launches();
+        if (cst != LQCD_OK) break;
+        ce = cudaEventRecord(ev[i], side[i]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, ev[i], 0);
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(cs, &g);
+      if (cst != LQCD_OK) { if (g) cudaGraphDestroy(g); return cst; }
+      if (ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_error(ce, "batch capture"); }
+      if (ee != cudaSuccess) return cuda_error(ee, "end capture");
+      cleanup.g = g;
+      LQCD_CUDA(cudaGraphInstantiate(&cleanup.ex, g, 0), "graph instantiate");
+      graph_key = key;
+    }
+    LQCD_CUDA(cudaGraphLaunch(cleanup.ex, s), "graph launch");
+    for (int i = 0; i < nlat; ++i)
+      if (running[i]) {
+        jobs[i].restarts += 1;
+        jobs[i].pending_k = true;
+        jobs[i].nl += jobs[i].cycle_launches();
+      }
+    ++rounds;
+  }
+  lqcd_status worst = LQCD_OK;
+  for (auto& j : jobs) {
+    st = j.finish();
+    if (st < 0) return st;
+    if (st != LQCD_OK) worst = st;
+  }
+  (void)rounds;
+  return worst;
 }
 
 }  // extern "C"

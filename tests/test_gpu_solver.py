@@ -150,3 +150,35 @@ def test_bf16_basis_solve(op):
     rel = oracle_relres(U, m0, c_sw, b, x)
     assert np.all(rel <= 1e-10), rel
     lat.close()
+
+
+def test_uneven_multi_lattice_batch_solve():
+    """Three lattices of different size, mass, gauge roughness and rhs count solved as one batch:
+    every rhs meets tol with the oracle's operator, the per-lattice results equal the single
+    solves' to rounding, and the lattices needing fewer restarts retire first."""
+    specs = [((4, 4, 4, 4), 0.2, 0.05, 2), ((8, 8, 8, 8), 0.3, -0.15, 4), ((8, 4, 4, 8), 0.4, 0.0, 3)]
+    lats, Us, bs, xs = [], [], [], []
+    for k, (dims, eps, m0, nr) in enumerate(specs):
+        U = syn.gauge_field(dims, "exp", eps, seed=3000 + k)
+        lat = lq.Lattice(dims)
+        lat.set_gauge(torch.from_numpy(U).cuda())
+        lat.set_clover(m0, 1.0)
+        lats.append(lat)
+        Us.append(U)
+        bs.append(torch.from_numpy(syn.gaussian_spinors(dims, nr, 3100 + k)).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+    res = lq.solve_batch(lats, bs, xs, [s[3] for s in specs], op=lq.OP_SCHUR, precision=lq.C64, restart_len=16,
+                         tol=1e-10)
+    torch.cuda.synchronize()
+    for k, (dims, eps, m0, nr) in enumerate(specs):
+        assert res[k].status == lq.OK, res[k]
+        rel = oracle_relres(Us[k], m0, 1.0, bs[k].cpu().numpy(), xs[k].cpu().numpy())
+        assert np.all(rel <= 1e-10), (k, rel)
+        x1 = torch.zeros_like(bs[k])
+        r1 = lats[k].solve(bs[k], x1, nr, op=lq.OP_SCHUR, precision=lq.C64, restart_len=16, tol=1e-10)
+        torch.cuda.synchronize()
+        assert r1.iterations == res[k].iterations and r1.restarts == res[k].restarts
+        assert torch.allclose(x1, xs[k], rtol=0, atol=1e-12 * float(x1.abs().max()))
+    assert len({r.restarts for r in res}) > 1      # uneven: the lattices retire at different rounds
+    for lat in lats:
+        lat.close()
