@@ -203,8 +203,14 @@ typedef struct {
   int restart_len;    /* m, 1..64 */
   int max_restarts;   /* >= 1 */
   double tol;         /* stop when ||b - D x|| <= tol ||b|| (true residual, per rhs) */
-  double inner_tol;   /* cycle stops when its Arnoldi estimate <= inner_tol * ||r_restart||
-                         (0: default 1e-5 for C64, none for C128); never below tol ||b|| */
+  double inner_tol;   /* C64 / BF16S (nested refinement): an inner solve on the correction
+                         equation D e = r_outer runs restarted FP32 cycles, each started
+                         from the FP32-computed residual r_outer - D (x - x_outer), until
+                         that residual is <= inner_tol * ||r_outer|| or stops decreasing;
+                         then the FP64 residual r_outer = b - D x is recomputed. A cycle
+                         stops when its Arnoldi estimate reaches that bound (never below
+                         tol ||b|| / 2). 0: default 1e-4. C128: unused (every restart
+                         recomputes the FP64 residual) */
   int x0_given;       /* 1: x holds the initial guess; 0: start from x = 0 */
   int use_graph;      /* 1: replay each Arnoldi cycle as a captured CUDA graph */
   int reorth;         /* 1: CGS2 (default); 0: one classical Gram-Schmidt pass */
@@ -214,7 +220,7 @@ typedef struct {
 
 typedef struct {
   int status;            /* LQCD_OK or LQCD_NOT_CONVERGED */
-  int restarts;          /* FP64 restarts (true-residual evaluations after the first) */
+  int restarts;          /* Arnoldi cycles (GMRES(m) restarts) that ran */
   int iterations;        /* Arnoldi steps, max over rhs */
   double seconds;        /* host wall time of the call */
   double relres_max;     /* max over rhs of the final ||b - D x|| / ||b|| (full operator) */
@@ -227,15 +233,17 @@ typedef struct {
   /* optional per-rhs outputs (host arrays of nrhs entries, may be NULL) */
   int* iters_per_rhs;
   double* relres_per_rhs;
+  int outer_steps;       /* FP64 true-residual evaluations r = b - D x (the first included) */
 } lqcd_solve_stats;
 
 /* Batched restarted GMRES (Algorithm 2), each rhs independent, optionally on the
  * odd-even Schur system (Sec. III-A-2). b, x: host or device (detected),
  * canonical complex128 [nrhs][V][4][3]; x is overwritten with the solution
  * (and read as the initial guess when x0_given). The true residual is
- * recomputed in FP64 at every restart, each rhs retires once it meets tol,
- * and the final full-operator residual is reported in stats. Synchronises
- * `stream` once per restart. Returns LQCD_NOT_CONVERGED if max_restarts is
+ * recomputed in FP64 at every restart (C128) or after every inner solve (C64,
+ * BF16S: mixed-precision iterative refinement, see inner_tol), each rhs retires
+ * once it meets tol, and the final full-operator residual is reported in stats.
+ * Synchronises `stream` once per restart. Returns LQCD_NOT_CONVERGED if max_restarts is
  * reached, LQCD_ERR_NONFINITE if b or a residual norm is not finite.
  * stats: host, may be NULL. nrhs: 1..64. */
 lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* params, int nrhs,

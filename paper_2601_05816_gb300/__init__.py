@@ -49,6 +49,7 @@ class SolveStats(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong),
         ("iters_per_rhs", ctypes.POINTER(ctypes.c_int)),
         ("relres_per_rhs", ctypes.POINTER(ctypes.c_double)),
+        ("outer_steps", ctypes.c_int),
     ]
 
 
@@ -149,6 +150,7 @@ class SolveResult:
     kernel_launches: int
     iters_per_rhs: list
     relres_per_rhs: list
+    outer_steps: int = 0
 
 
 class Lattice:
@@ -293,7 +295,7 @@ class Lattice:
                                              ctypes.byref(st), _stream(stream)), "lqcd_solve")
         return SolveResult(status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                            st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
-                           st.kernel_launches, list(its), list(rel))
+                           st.kernel_launches, list(its), list(rel), st.outer_steps)
 
 
 def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
@@ -324,5 +326,5 @@ def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = 
         st = stats[i]
         out.append(SolveResult(st.status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                                st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
-                               st.kernel_launches, list(per_its[i]), list(per_rel[i])))
+                               st.kernel_launches, list(per_its[i]), list(per_rel[i]), st.outer_steps))
     return out

@@ -556,14 +556,16 @@ cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, 
 
 // ------------------------------------------------------------------ small streaming kernels
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-sub_norm_kernel(int64_t n, int nrhs, const double2* __restrict__ b, const double2* __restrict__ t,
+sub_norm_kernel(int64_t n, int nrhs, const double2* __restrict__ b, const T* __restrict__ t,
                 double2* __restrict__ r, double2* __restrict__ partials) {
   double nn = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    const double2 bv = b[e], tv = t[e];
-    const double2 rv = make_double2(bv.x - tv.x, bv.y - tv.y);
+    const double2 bv = b[e];
+    const T tv = t[e];
+    const double2 rv = make_double2(bv.x - (double)tv.x, bv.y - (double)tv.y);
     r[e] = rv;
     nn += rv.x * rv.x + rv.y * rv.y;
   }
@@ -572,12 +574,34 @@ sub_norm_kernel(int64_t n, int nrhs, const double2* __restrict__ b, const double
 }
 
 cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
-                            void* partials, void* out, cudaStream_t stream) {
-  sub_norm_kernel<<<plan.blocks, plan.threads, 0, stream>>>(
-      n, plan.nrhs, (const double2*)b, (const double2*)t, (double2*)r, (double2*)partials);
+                            void* partials, void* out, cudaStream_t stream, bool t_f32) {
+  if (t_f32)
+    sub_norm_kernel<float2><<<plan.blocks, plan.threads, 0, stream>>>(
+        n, plan.nrhs, (const double2*)b, (const float2*)t, (double2*)r, (double2*)partials);
+  else
+    sub_norm_kernel<double2><<<plan.blocks, plan.threads, 0, stream>>>(
+        n, plan.nrhs, (const double2*)b, (const double2*)t, (double2*)r, (double2*)partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_reduce(plan.blocks, plan.nrhs, partials, out, nullptr, stream);
+}
+
+__global__ void __launch_bounds__(256)
+diff_to_f32_kernel(int64_t n, const double2* __restrict__ a, const double2* __restrict__ b,
+                   float2* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const double2 av = a[e], bv = b[e];
+    out[e] = make_float2((float)(av.x - bv.x), (float)(av.y - bv.y));
+  }
+}
+
+cudaError_t launch_diff_to_f32(int64_t n, const void* a, const void* b, void* out, cudaStream_t stream) {
+  const int threads = 256;
+  int64_t blocks = (n + threads - 1) / threads;
+  if (blocks > 65535 * 16) blocks = 65535 * 16;
+  diff_to_f32_kernel<<<(int)blocks, threads, 0, stream>>>(n, (const double2*)a, (const double2*)b, (float2*)out);
+  return cudaGetLastError();
 }
 
 template <typename C>

@@ -67,9 +67,11 @@ cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, 
                            cudaStream_t stream, const double* oscale = nullptr, bool basis_bf16 = false,
                            void* wout = nullptr);
 
-// r = b - t (all FP64) with out[0][r] = ||r||^2.
+// r = b - t (b, r FP64; t FP64, or FP32 when t_f32) with out[0][r] = ||r||^2.
 cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,
-                            void* partials, void* out, cudaStream_t stream);
+                            void* partials, void* out, cudaStream_t stream, bool t_f32 = false);
+// out = (FP32) (a - b), a and b FP64.
+cudaError_t launch_diff_to_f32(int64_t n, const void* a, const void* b, void* out, cudaStream_t stream);
 // ||v||^2 per rhs, out[0][r]; v in FP64 or FP32.
 cudaError_t launch_norm2(bool f64, const BlasPlan& plan, int64_t n, const void* v, void* partials,
                          void* out, cudaStream_t stream);

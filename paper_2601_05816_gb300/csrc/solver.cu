@@ -408,6 +408,17 @@ struct SolveJob {
   int restarts = 0;
   bool pending_k = false;
   bool finished = false;
+  // nested refinement (FP32 / BF16 inner): inner restarts start from the FP32 residual
+  // of the correction equation, r_outer - D (x - x_outer); an FP64 residual follows
+  // each inner solve
+  bool nested = false;
+  bool outer_next = true;   // the next residual is the FP64 one
+  bool last_outer = true;   // the residual being decided was the FP64 one
+  int inner_cycles = 0;
+  int outer_steps = 0;
+  void *x_outer = nullptr, *r_outer = nullptr, *e32 = nullptr, *t32 = nullptr;
+  std::vector<double> rn_prev;
+  std::vector<char> active_outer, inner_done;
   long long nl = 0;  // kernel launches of this solve
   double op_bytes_inner = 0.0;
   lqcd_status result = LQCD_NOT_CONVERGED;
@@ -415,7 +426,9 @@ struct SolveJob {
   lqcd_status setup(lqcd_ctx c, const lqcd_solve_params* params, int nr, const void* bb, void* xx,
                     lqcd_solve_stats* st_out, cudaStream_t stream);
   lqcd_status enqueue_residual();
-  lqcd_status decide(bool* run);   // after the stream has been synchronised
+  // after the stream has been synchronised: *run = a cycle follows; with neither run
+  // nor finished, the next residual (the FP64 one) is due before the next cycle
+  lqcd_status decide(bool* run);
   lqcd_status enqueue_cycle(cudaStream_t cs, bool allow_graph);
   lqcd_status finish();
   // kernels of one restart cycle: cycle_init, v0, per step (operator, Gram-Schmidt
@@ -442,7 +455,7 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   bf16 = P.precision == LQCD_BF16S;
   m = P.restart_len;
   reorth = P.reorth != 0 || bf16;
-  inner_tol = P.inner_tol > 0.0 ? P.inner_tol : (f64_inner ? 0.0 : 1e-5);
+  inner_tol = P.inner_tol > 0.0 ? P.inner_tol : (f64_inner ? 0.0 : 1e-4);
   n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
   n_half = n_full / 2;
   n_sys = eo ? n_half : n_full;
@@ -479,6 +492,16 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     else if ((st = workspace(ctx, "schur_tmp32", (size_t)n_half * sizeof(float2), &B.tmp_even_in)) != LQCD_OK)
       return st;
   }
+  nested = !f64_inner;
+  if (nested) {
+    if ((st = workspace(ctx, "solve_x_outer", (size_t)n_sys * sizeof(double2), &x_outer)) != LQCD_OK) return st;
+    if ((st = workspace(ctx, "solve_r_outer", (size_t)n_sys * sizeof(double2), &r_outer)) != LQCD_OK) return st;
+    if ((st = workspace(ctx, "solve_e32", (size_t)n_sys * sizeof(float2), &e32)) != LQCD_OK) return st;
+    if ((st = workspace(ctx, "solve_t32", (size_t)n_sys * sizeof(float2), &t32)) != LQCD_OK) return st;
+  }
+  rn_prev.assign(nrhs, 0.0);
+  active_outer.assign(nrhs, 0);
+  inner_done.assign(nrhs, 1);
   B.plan = blas_plan(n_sys, nrhs, ctx->num_sms);
   B.plan.wait_flag = wait_flag(ctx);
   const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
@@ -561,22 +584,42 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   return LQCD_OK;
 }
 
-// True residual r = b - D x in FP64 and its norms copied to the pinned staging area.
+// The residual of the next restart and its norms, copied to the pinned staging area:
+// the FP64 true residual r = b - D x (then, nested, x_outer = x and r_outer = r), or
+// (nested, inner restart) r = r_outer - D_32 fl32(x - x_outer) with the FP32 operator.
 lqcd_status SolveJob::enqueue_residual() {
   lqcd_status st;
-  if ((st = apply_operator(ctx, P.op, true, nrhs, sys_x, t64, tmp64, nullptr, s)) != LQCD_OK) return st;
-  LQCD_CUDA(launch_sub_norm(B.plan, n_sys, sys_b, t64, r64, B.partials, B.hn, s), "residual");
+  last_outer = !nested || outer_next;
+  if (last_outer) {
+    if ((st = apply_operator(ctx, P.op, true, nrhs, sys_x, t64, tmp64, nullptr, s)) != LQCD_OK) return st;
+    LQCD_CUDA(launch_sub_norm(B.plan, n_sys, sys_b, t64, r64, B.partials, B.hn, s), "residual");
+    nl += eo ? 4 : 3;  // FP64 operator + residual kernel + reduction
+    if (nested) {
+      LQCD_CUDA(cudaMemcpyAsync(x_outer, sys_x, (size_t)n_sys * sizeof(double2), cudaMemcpyDeviceToDevice, s),
+                "save x");
+      LQCD_CUDA(cudaMemcpyAsync(r_outer, r64, (size_t)n_sys * sizeof(double2), cudaMemcpyDeviceToDevice, s),
+                "save r");
+    }
+  } else {
+    LQCD_CUDA(launch_diff_to_f32(n_sys, sys_x, x_outer, e32, s), "correction");
+    if ((st = apply_operator(ctx, P.op, false, nrhs, e32, t32, B.tmp_even_in, nullptr, s)) != LQCD_OK) return st;
+    LQCD_CUDA(launch_sub_norm(B.plan, n_sys, r_outer, t32, r64, B.partials, B.hn, s, true), "inner residual");
+    nl += eo ? 5 : 4;  // difference, FP32 operator, residual kernel + reduction
+  }
   LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read rn");
   hs->wait_err = 0;
   if (B.plan.wait_flag)
     LQCD_CUDA(cudaMemcpyAsync(&hs->wait_err, B.plan.wait_flag, sizeof(int), cudaMemcpyDeviceToHost, s), "read flag");
-  nl += eo ? 4 : 3;  // FP64 operator + residual kernel + reduction
   return LQCD_OK;
 }
 
-// Host decision of one restart (the residual norms have arrived): retire the rhs
-// that meet tol, set the cycle thresholds and starting norms, upload them.
+// Host decision of one restart (the residual norms have arrived). After the FP64
+// residual: retire the rhs that meet tol, set each cycle threshold from it. After
+// an inner residual: an rhs ends its inner solve when the residual reaches the
+// threshold, no longer decreases (less than 10% per cycle: the FP32 operator's
+// rounding floor) or after kMaxInner cycles; when all have, the FP64 residual is due.
 lqcd_status SolveJob::decide(bool* run) {
+  constexpr int kMaxInner = 16;
   *run = false;
   if (pending_k) {
     int kmax = 0;
@@ -591,29 +634,59 @@ lqcd_status SolveJob::decide(bool* run) {
     return set_error(LQCD_ERR_CUDA, "lqcd_solve: a Gram-Schmidt pipeline wait timed out (device flag %d)",
                      hs->wait_err);
   int n_active = 0;
-  for (int r = 0; r < nrhs; ++r) {
-    const double rn = std::sqrt(hs->rn2[2 * r]);
-    if (!std::isfinite(rn))
-      return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: residual of rhs %d is not finite", r);
-    relres[r] = bnorm[r] > 0.0 ? rn / bnorm[r] : 0.0;
-    const bool act = bnorm[r] > 0.0 && rn > P.tol * bnorm[r];
-    hs->active[r] = act ? 1 : 0;
-    hs->beta0[r] = act ? rn : 1.0;
-    // cycle target: half the tolerance (so the true residual, which the Arnoldi
-    // estimate approximates, lands below tol), or the inner relative reduction
-    double thr = 0.5 * P.tol * bnorm[r];
-    if (inner_tol > 0.0) thr = std::max(thr, inner_tol * rn);
-    hs->thr[r] = thr;
-    n_active += act;
-  }
-  if (n_active == 0) {
-    result = LQCD_OK;
-    finished = true;
-    return LQCD_OK;
-  }
-  if (restarts >= P.max_restarts) {
-    finished = true;
-    return LQCD_OK;
+  if (last_outer) {
+    ++outer_steps;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rn = std::sqrt(hs->rn2[2 * r]);
+      if (!std::isfinite(rn))
+        return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: residual of rhs %d is not finite", r);
+      relres[r] = bnorm[r] > 0.0 ? rn / bnorm[r] : 0.0;
+      const bool act = bnorm[r] > 0.0 && rn > P.tol * bnorm[r];
+      active_outer[r] = act ? 1 : 0;
+      inner_done[r] = act ? 0 : 1;
+      rn_prev[r] = rn;
+      hs->active[r] = act ? 1 : 0;
+      hs->beta0[r] = act ? rn : 1.0;
+      // cycle target: half the tolerance (so the true residual, which the Arnoldi
+      // estimate approximates, lands below tol), or the inner relative reduction
+      double thr = 0.5 * P.tol * bnorm[r];
+      if (inner_tol > 0.0) thr = std::max(thr, inner_tol * rn);
+      hs->thr[r] = thr;
+      n_active += act;
+    }
+    if (n_active == 0) {
+      result = LQCD_OK;
+      finished = true;
+      return LQCD_OK;
+    }
+    if (restarts >= P.max_restarts) {
+      finished = true;
+      return LQCD_OK;
+    }
+    outer_next = false;
+    inner_cycles = 0;
+  } else {
+    ++inner_cycles;
+    for (int r = 0; r < nrhs; ++r) {
+      hs->active[r] = 0;
+      hs->beta0[r] = 1.0;
+      if (!active_outer[r] || inner_done[r]) continue;
+      const double rn = std::sqrt(hs->rn2[2 * r]);
+      if (!std::isfinite(rn))
+        return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: inner residual of rhs %d is not finite", r);
+      if (rn <= hs->thr[r] || rn > 0.9 * rn_prev[r] || inner_cycles >= kMaxInner) {
+        inner_done[r] = 1;
+        continue;
+      }
+      rn_prev[r] = rn;
+      hs->active[r] = 1;
+      hs->beta0[r] = rn;
+      ++n_active;
+    }
+    if (n_active == 0 || restarts >= P.max_restarts) {
+      outer_next = true;  // the FP64 residual decides convergence (or the end)
+      return LQCD_OK;
+    }
   }
   LQCD_CUDA(cudaMemcpyAsync(B.st.active, hs->active, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s), "up");
   LQCD_CUDA(cudaMemcpyAsync(B.st.thr, hs->thr, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s), "up");
@@ -672,6 +745,7 @@ lqcd_status SolveJob::finish() {
     stats->ortho_launches = prof.gs_n;
     stats->ortho_bytes = prof.gs_bytes;
     stats->kernel_launches = nl;
+    stats->outer_steps = outer_steps;
     if (stats->iters_per_rhs) for (int r = 0; r < nrhs; ++r) stats->iters_per_rhs[r] = iters[r];
     if (stats->relres_per_rhs) for (int r = 0; r < nrhs; ++r) stats->relres_per_rhs[r] = relres[r];
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -743,7 +817,8 @@ lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* P, int nrhs, const
     LQCD_CUDA(cudaStreamSynchronize(s), "sync residual");
     bool run = false;
     if ((st = job.decide(&run)) != LQCD_OK) return st;
-    if (!run) break;
+    if (job.finished) break;
+    if (!run) continue;   // the FP64 residual is due first
     if ((st = job.enqueue_cycle(s, true)) != LQCD_OK) return st;
   }
   return job.finish();
@@ -803,7 +878,10 @@ lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_pa
       n_run += run;
       key += run ? '1' : '0';
     }
-    if (n_run == 0) break;
+    bool all_finished = true;
+    for (auto& j : jobs) all_finished = all_finished && j.finished;
+    if (all_finished) break;
+    if (n_run == 0) continue;   // only FP64 residuals are due this round
     if (key != graph_key) {   // the set of running lattices changed: capture the round anew
       if (cleanup.ex) { cudaGraphExecDestroy(cleanup.ex); cleanup.ex = nullptr; }
       if (cleanup.g) { cudaGraphDestroy(cleanup.g); cleanup.g = nullptr; }
