@@ -18,6 +18,10 @@ The oracle is plain numpy in complex128, written from the paper's definitions:
   (Schur) solve.
 * ``dense``: a brute-force dense matrix of D built entry by entry with explicit
   site loops, for tiny lattices.
+* ``adjoint``: the adjoint operator D^dagger, the adjoint solve and the
+  gradients dL/db and dL/dU (hopping and clover-leaf parts) of
+  L = sum_i Re <eta_i, D^{-1} b_i> (the task's differentiable solve; not in the
+  paper), pinned by finite differences of the dense operator's loss.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, invariants, brute force, library
