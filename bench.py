@@ -44,12 +44,24 @@ WORKLOADS = {
                   c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, restart=32, tol=1e-10),
     "solve-large": dict(name="eo-gmres32-mixed 32^3x64 clover nrhs=12", dims=(64, 32, 32, 32), eps=0.25, m0=-0.3,
                         c_sw=1.0, nrhs=12, gauge_seed=2000, rhs_seed=2001, restart=32, tol=1e-10),
+    # differentiable solve: one step = forward solve + adjoint solve + link force (the gradient of
+    # L = sum_i Re <eta_i, D^{-1} b_i> in b and U)
+    "adjoint": dict(name="adjoint eo-gmres32-mixed 16^4 clover nrhs=8 (dL/db, dL/dU)", dims=(16, 16, 16, 16), eps=0.3,
+                    m0=-0.05, c_sw=1.0, nrhs=8, gauge_seed=4001, rhs_seed=4002, restart=32, tol=1e-10,
+                    kind="adjoint"),
     # single-kernel workloads (one step = one launch group), also the small cases for ncu captures
     "apply": dict(name="schur-apply c64 16^3x32 clover nrhs=16", dims=(32, 16, 16, 16), eps=0.3, m0=-0.2,
                   c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, kind="apply"),
     "ortho": dict(name="cgs2-step c64 16^3x32 odd sites nrhs=16 nvec=16", dims=(32, 16, 16, 16), eps=0.3,
                   m0=-0.2, c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, kind="ortho", nvec=16),
 }
+
+
+# DRAM bytes (read + write) per CGS2 step of the timed solve, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a full 32-step Arnoldi cycle, i.e.
+# 96 streaming Gram-Schmidt launches, of the default workload; the summary is
+# profiles/gs_stream_cgs2_c64_16x16x16x32_nrhs16.md. Workloads not captured report null.
+GS_TRAFFIC_PER_STEP = {("solve", "c64"): 5.36e9}
 
 
 def measured_peaks():
@@ -334,6 +346,78 @@ def run_kernel_workload(args, w):
         dist.destroy_process_group()
 
 
+def run_adjoint_workload(args, w):
+    """One step = x = D^{-1} b (FP32 inner, FP64 refinement), lambda = D^{-dagger} eta, dL/dU (lqcd_force)."""
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2601_05816_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    import paper_2601_05816_gb300 as lq
+    import synthetic as syn
+    lq.load()
+    dims, nrhs = w["dims"], w["nrhs"]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U_d = torch.from_numpy(syn.gauge_field(dims, "exp", w["eps"], seed=w["gauge_seed"])).cuda()
+    b_d = torch.from_numpy(syn.gaussian_spinors(dims, nrhs, rank_rhs_seed(w["rhs_seed"], rank))).cuda()
+    eta_d = torch.from_numpy(syn.gaussian_spinors(dims, nrhs, rank_rhs_seed(w["rhs_seed"], rank) + 1)).cuda()
+    lat = lq.Lattice(dims, time_bc=-1)
+    kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=w["restart"], tol=w["tol"],
+              max_restarts=args.max_restarts)
+    s = torch.cuda.current_stream()
+
+    def step():
+        U = U_d.clone().requires_grad_(True)
+        b = b_d.clone().requires_grad_(True)
+        x = lq.solve_differentiable(lat, U, b, w["m0"], w["c_sw"], **kw)
+        (torch.conj(eta_d) * x).real.sum().backward()
+        return U.grad, b.grad
+
+    for _ in range(args.warmup):
+        step()
+    # force kernel alone (the solves dominate the step)
+    x = torch.zeros_like(b_d)
+    lam = torch.zeros_like(b_d)
+    lat.solve(b_d, x, nrhs, **kw)
+    lat.solve(eta_d, lam, nrhs, dagger=True, **kw)
+    G = torch.empty_like(U_d)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.force(nrhs, x, lam, G)
+    e0.record(s)
+    for _ in range(5):
+        lat.force(nrhs, x, lam, G)
+    e1.record(s)
+    torch.cuda.synchronize()
+    force_ms = e0.elapsed_time(e1) / 5
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            gU, gb = step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(world)
+    t = allreduce_max(world, e0.elapsed_time(e1) * 1e-3)
+    line = {"metric": METRIC, "value": world * V * nrhs * args.steps / t, "unit": "site·rhs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32 inner / fp64 refinement; fp64 force", "data": "synthetic",
+            "config": {"workload": w["name"], "m0": w["m0"], "c_sw": w["c_sw"],
+                       "step": "forward solve + adjoint (gamma5) solve + link force, via torch autograd"},
+            "force_kernel_ms": force_ms, "grad_norms": {"dL_dU": float(gU.abs().max()), "dL_db": float(gb.abs().max())},
+            "clocks": clk.summary()}
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -401,13 +485,15 @@ def run_gpu(args, w):
     gs_ms = sum(r.ortho_ms for r in results)
     if gs_ms >= op_ms:
         dom = dict(kernel="gs_pass (CGS2 step: 3 fused passes)", ms=gs_ms, n=sum(r.ortho_launches for r in results),
-                   bytes=sum(r.ortho_bytes for r in results))
+                   bytes=sum(r.ortho_bytes for r in results),
+                   traffic=GS_TRAFFIC_PER_STEP.get((args.workload, args.precision))
+                   if "m0_prescribed" not in w else None)
     else:
         dom = dict(kernel="dslash (Schur apply: passes A + B)", ms=op_ms, n=sum(r.op_launches for r in results),
-                   bytes=sum(r.op_bytes for r in results))
+                   bytes=sum(r.op_bytes for r in results), traffic=None)
     achieved = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9 if dom["ms"] > 0 else float("nan")
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": dom["traffic"],
                 "launches": dom["n"], "avg_launch_ms": dom["ms"] / max(dom["n"], 1),
                 "bytes_per_launch": dom["bytes"] / max(dom["n"], 1),
                 "share_of_step": (dom["ms"] * 1e-3) / t_local,
@@ -557,6 +643,8 @@ def main():
         run_reference(args, w)
     elif w.get("kind") in ("apply", "ortho"):
         run_kernel_workload(args, w)
+    elif w.get("kind") == "adjoint":
+        run_adjoint_workload(args, w)
     else:
         run_gpu(args, w)
 

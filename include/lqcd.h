@@ -216,6 +216,10 @@ typedef struct {
   int reorth;         /* 1: CGS2 (default); 0: one classical Gram-Schmidt pass */
   int profile;        /* 1: time operator and Gram-Schmidt launches with CUDA events
                          (use_graph is then ignored) */
+  int dagger;         /* 1: solve the adjoint system D^dagger x = b instead, as
+                         gamma5 D^{-1} gamma5 b (D^dagger = gamma5 D gamma5, Sec. III-A-1's
+                         operator is gamma5-Hermitian); tol and the reported residuals
+                         refer to D^dagger */
 } lqcd_solve_params;
 
 typedef struct {
@@ -248,6 +252,22 @@ typedef struct {
  * stats: host, may be NULL. nrhs: 1..64. */
 lqcd_status lqcd_solve(lqcd_ctx ctx, const lqcd_solve_params* params, int nrhs,
                        const void* b, void* x, lqcd_solve_stats* stats, void* stream);
+
+/* Gradient of a loss L = sum_i Re <eta_i, x_i> with x_i = D^{-1} b_i with respect to
+ * the gauge links, given x and lambda_i = D^{-dagger} eta_i (an lqcd_solve with dagger = 1
+ * on eta): dL = -Re <lambda, (dD) x>, from the hopping terms of D (outer products
+ * of the projected spinors pi^-+ x with lambda) and, when c_sw != 0, from the clover
+ * term (the derivative of every plaquette leaf of Q_mu,nu). Not in the paper (its
+ * solver has no adjoint). grad_U is PyTorch's gradient of a real loss for complex
+ * entries: dL = Re sum conj(grad_U) dU over the entries of U treated as independent
+ * complex numbers (the su(3) force is TA(U grad_U^dagger)). Uses the context's gauge
+ * field and c_sw (set_gauge, set_clover first).
+ * x, lambda: device, canonical complex128 [nrhs][V][4][3]; grad_U: device, canonical
+ * complex128 [V][4][3][3] (the layout of lqcd_set_gauge's input), overwritten.
+ * Library workspace: V * 13.5 KB for the clover leaves. Deterministic (fixed-order
+ * sums, no atomics). nrhs: 1..256. */
+lqcd_status lqcd_force(lqcd_ctx ctx, int nrhs, const void* x, const void* lambda, void* grad_U,
+                       void* stream);
 
 /* Batched GMRES over several lattices of uneven size (one lattice context per
  * entry, distinct contexts): the solve of lqcd_solve for every lattice i with

@@ -36,7 +36,7 @@ class SolveParams(ctypes.Structure):
         ("op", ctypes.c_int), ("precision", ctypes.c_int), ("restart_len", ctypes.c_int),
         ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("x0_given", ctypes.c_int), ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int),
-        ("profile", ctypes.c_int),
+        ("profile", ctypes.c_int), ("dagger", ctypes.c_int),
     ]
 
 
@@ -72,6 +72,7 @@ _SIGS = {
     "lqcd_schur_reconstruct": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP]),
     "lqcd_orthogonalise": (_I, [_VP, _I, _I, _I, _I, _VP, _VP, _VP, _VP, _I, _VP]),
     "lqcd_solve": (_I, [_VP, ctypes.POINTER(SolveParams), _I, _VP, _VP, ctypes.POINTER(SolveStats), _VP]),
+    "lqcd_force": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "lqcd_tune": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _VP]),
     "lqcd_solve_batch": (_I, [_I, ctypes.POINTER(_VP), ctypes.POINTER(SolveParams), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(SolveStats), _VP]),
@@ -282,10 +283,12 @@ class Lattice:
 
     def solve(self, b, x, nrhs: int, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
               max_restarts: int = 200, tol: float = 1e-10, inner_tol: float = 0.0, x0_given: bool = False,
-              use_graph: bool = True, reorth: bool = True, profile: bool = False, stream=None) -> SolveResult:
-        """Batched GMRES on D x = b; b and x complex128 canonical [nrhs][V][4][3], host (numpy) or device."""
+              use_graph: bool = True, reorth: bool = True, profile: bool = False, dagger: bool = False,
+              stream=None) -> SolveResult:
+        """Batched GMRES on D x = b (dagger: D^dagger x = b); b and x complex128 canonical [nrhs][V][4][3],
+        host (numpy) or device."""
         p = SolveParams(op, precision, restart_len, max_restarts, tol, inner_tol, int(x0_given), int(use_graph),
-                        int(reorth), int(profile))
+                        int(reorth), int(profile), int(dagger))
         its = (ctypes.c_int * nrhs)()
         rel = (ctypes.c_double * nrhs)()
         st = SolveStats()
@@ -296,6 +299,13 @@ class Lattice:
         return SolveResult(status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                            st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
                            st.kernel_launches, list(its), list(rel), st.outer_steps)
+
+
+    def force(self, nrhs: int, x, lam, grad_U, stream=None) -> None:
+        """dL/dU for L = sum_i Re <eta_i, x_i>, x = D^{-1} b, lam = D^{-dagger} eta (lqcd_force): device complex128
+        x, lam [nrhs][V][4][3] and grad_U [V][4][3][3] (overwritten)."""
+        _check(self._lib.lqcd_force(self._h, int(nrhs), _ptr(x), _ptr(lam), _ptr(grad_U), _stream(stream)),
+               "lqcd_force")
 
 
 def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
@@ -310,7 +320,7 @@ def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = 
     tols = list(tol) if isinstance(tol, (list, tuple)) else [tol] * n
     ctxs = (ctypes.c_void_p * n)(*[lat.handle.value for lat in lattices])
     params = (SolveParams * n)(*[SolveParams(op, precision, restart_len, max_restarts, tols[i], inner_tol, 0,
-                                             int(use_graph), int(reorth), 0) for i in range(n)])
+                                             int(use_graph), int(reorth), 0, 0) for i in range(n)])
     nr = (ctypes.c_int * n)(*[int(v) for v in nrhs])
     bp = (ctypes.c_void_p * n)(*[_ptr(v) for v in bs])
     xp = (ctypes.c_void_p * n)(*[_ptr(v) for v in xs])
@@ -328,3 +338,59 @@ def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = 
                                st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
                                st.kernel_launches, list(per_its[i]), list(per_rel[i]), st.outer_steps))
     return out
+
+
+def _autograd_function():
+    import torch
+
+    class DiracSolve(torch.autograd.Function):
+        """x = D[U]^{-1} b for a block of rhs, differentiable in b and U.
+
+        Backward: the adjoint solve lam = D^{-dagger} g (g the incoming gradient of x; the
+        Krylov basis is recomputed, not stored), dL/db = lam and dL/dU from lqcd_force."""
+
+        @staticmethod
+        def forward(ctx, b, U, lattice, m0, c_sw, kw):
+            lattice.set_gauge(U.detach().contiguous())
+            lattice.set_clover(m0, c_sw)
+            x = torch.zeros_like(b)
+            res = lattice.solve(b.detach().contiguous(), x, b.shape[0], **kw)
+            if res.status != OK:
+                raise LqcdError(res.status, f"forward solve did not converge: {res}")
+            ctx.lattice, ctx.m0, ctx.c_sw, ctx.kw = lattice, m0, c_sw, kw
+            ctx.save_for_backward(U, x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            U, x = ctx.saved_tensors
+            lat = ctx.lattice
+            lat.set_gauge(U.detach().contiguous())
+            lat.set_clover(ctx.m0, ctx.c_sw)
+            g = gx.detach().contiguous()
+            lam = torch.zeros_like(g)
+            res = lat.solve(g, lam, g.shape[0], dagger=True, **ctx.kw)
+            if res.status != OK:
+                raise LqcdError(res.status, f"adjoint solve did not converge: {res}")
+            gU = None
+            if ctx.needs_input_grad[1]:
+                gU = torch.empty(U.shape, dtype=U.dtype, device=U.device)
+                lat.force(g.shape[0], x, lam, gU)
+            return (lam if ctx.needs_input_grad[0] else None), gU, None, None, None, None
+
+    return DiracSolve
+
+
+_DIRAC_SOLVE = None
+
+
+def solve_differentiable(lattice, U, b, m0: float, c_sw: float, **solve_kw):
+    """x = D^{-1} b (batched GMRES of lqcd_solve) as a torch autograd function of b and U.
+
+    U: device complex128 [V][4][3][3] (canonical), b: device complex128 [nrhs][V][4][3]; solve_kw as for
+    Lattice.solve (tol, precision, op, ...). Gradients: dL/db by one adjoint solve, dL/dU by lqcd_force.
+    """
+    global _DIRAC_SOLVE
+    if _DIRAC_SOLVE is None:
+        _DIRAC_SOLVE = _autograd_function()
+    return _DIRAC_SOLVE.apply(b, U, lattice, float(m0), float(c_sw), dict(solve_kw))

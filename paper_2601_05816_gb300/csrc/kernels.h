@@ -85,6 +85,9 @@ cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const d
 cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
                             int64_t vstride, const void* y, const int* kmax, void* x,
                             cudaStream_t stream, bool basis_bf16 = false);
+// force.cu: gamma5 = diag(-1, -1, 1, 1) in place on an FP64 packed block of n complex
+// elements (nrhs rhs, site tile 2^log_s).
+cudaError_t launch_gamma5_packed(int64_t n, int nrhs, int log_s, void* v, cudaStream_t s);
 // Widen / narrow copies between FP64 and FP32 packed blocks.
 cudaError_t launch_convert(bool to_f64, int64_t n, const void* src, void* dst, cudaStream_t stream);
 

@@ -447,7 +447,8 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   if (nrhs < 1 || nrhs > 64 || P.restart_len < 1 || P.restart_len > 64 || P.max_restarts < 1 ||
       !(P.tol > 0.0) || (P.op != LQCD_OP_FULL && P.op != LQCD_OP_SCHUR) ||
       (P.precision != LQCD_C64 && P.precision != LQCD_C128 && P.precision != LQCD_BF16S) ||
-      (P.precision == LQCD_BF16S && nrhs > 32 && (nrhs % 2 != 0 || nrhs > 64)))
+      (P.precision == LQCD_BF16S && nrhs > 32 && (nrhs % 2 != 0 || nrhs > 64)) ||
+      (P.dagger != 0 && P.dagger != 1))
     return set_error(LQCD_ERR_ARG,
                      "lqcd_solve: bad parameters (nrhs 1..64, 1..32 for BF16 storage, restart_len 1..64, tol > 0)");
   eo = P.op == LQCD_OP_SCHUR;
@@ -551,9 +552,13 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   // ---------------- inputs
   if (b_host) LQCD_CUDA(cudaMemcpyAsync(b_can, b, full64, cudaMemcpyHostToDevice, s), "upload b");
   if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, b_can, b64, s)) != LQCD_OK) return st;
+  const int log_s = layout_for(ctx, nrhs).log_s;
+  // adjoint system: D^dagger x = b is solved as D y = gamma5 b, x = gamma5 y
+  if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, b64, s), "gamma5 b");
   if (P.x0_given) {
     if (x_host) LQCD_CUDA(cudaMemcpyAsync(x_can, x, full64, cudaMemcpyHostToDevice, s), "upload x0");
     if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x_can, x64, s)) != LQCD_OK) return st;
+    if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, x64, s), "gamma5 x0");
   } else {
     LQCD_CUDA(cudaMemsetAsync(x64, 0, full64, s), "zero x");
   }
@@ -722,6 +727,8 @@ lqcd_status SolveJob::finish() {
   if ((st = apply_operator(ctx, LQCD_OP_FULL, true, nrhs, x64, t64, nullptr, nullptr, s)) != LQCD_OK) return st;
   LQCD_CUDA(launch_sub_norm(plan_full, n_full, b64, t64, r64, red_partials, B.hn, s), "final residual");
   LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read final");
+  if (P.dagger)
+    LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, layout_for(ctx, nrhs).log_s, x64, s), "gamma5 x");
   if ((st = lqcd_unpack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x64, x_can, s)) != LQCD_OK) return st;
   if (x_host) LQCD_CUDA(cudaMemcpyAsync(x, x_can, full64, cudaMemcpyDeviceToHost, s), "download x");
   LQCD_CUDA(cudaStreamSynchronize(s), "final sync");
