@@ -44,6 +44,12 @@ WORKLOADS = {
                   c_sw=1.0, nrhs=16, gauge_seed=1000, rhs_seed=1001, restart=32, tol=1e-10),
     "solve-large": dict(name="eo-gmres32-mixed 32^3x64 clover nrhs=12", dims=(64, 32, 32, 32), eps=0.25, m0=-0.3,
                         c_sw=1.0, nrhs=12, gauge_seed=2000, rhs_seed=2001, restart=32, tol=1e-10),
+    # uneven multi-lattice batch: one step = one lqcd_solve_batch over four lattices of different
+    # size, gauge roughness, mass and rhs count (eo GMRES(32), FP32 inner, FP64 refinement, 1e-10)
+    "batch": dict(name="uneven batch 8^4/12^4/16^4/16^3x32 nrhs 4/8/16/32 eo-gmres32-mixed", kind="batch",
+                  lattices=[((8, 8, 8, 8), 0.2, 0.05, 4), ((12, 12, 12, 12), 0.27, 0.0, 8),
+                            ((16, 16, 16, 16), 0.33, -0.05, 16), ((32, 16, 16, 16), 0.4, -0.1, 32)],
+                  c_sw=1.0, gauge_seed=3000, rhs_seed=3100, restart=32, tol=1e-10),
     # differentiable solve: one step = forward solve + adjoint solve + link force (the gradient of
     # L = sum_i Re <eta_i, D^{-1} b_i> in b and U)
     "adjoint": dict(name="adjoint eo-gmres32-mixed 16^4 clover nrhs=8 (dL/db, dL/dU)", dims=(16, 16, 16, 16), eps=0.3,
@@ -199,6 +205,10 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if "dims" not in w:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle arm for the {w['name']} workload; "
+                          "the default workload times the oracle"}), flush=True)
+        return
     V = w["dims"][0] * w["dims"][1] * w["dims"][2] * w["dims"][3]
     # projected time to solution of one rhs: per-iteration oracle cost x the GPU solve's
     # iteration count for this workload (fixed number recorded from the GPU run)
@@ -339,6 +349,85 @@ def run_kernel_workload(args, w):
         line["tuning"] = {"variant_ms_full_schur": tuning,
                           "chosen_schur": lat.kernel_variant(lq.C64, nrhs, lq.OP_SCHUR)}
     lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_batch_workload(args, w):
+    """One step = one lqcd_solve_batch over the workload's lattices; also the same solves one after another."""
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2601_05816_gb300 import _build
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    import paper_2601_05816_gb300 as lq
+    import synthetic as syn
+    lq.load()
+    lats, Us, bs, xs, nr, m0s = [], [], [], [], [], []
+    units = 0
+    for k, (dims, eps, m0, nrhs) in enumerate(w["lattices"]):
+        U = torch.from_numpy(syn.gauge_field(dims, "exp", eps, seed=w["gauge_seed"] + k)).cuda()
+        b = torch.from_numpy(syn.gaussian_spinors(dims, nrhs, rank_rhs_seed(w["rhs_seed"] + k, rank))).cuda()
+        lat = lq.Lattice(dims, time_bc=-1)
+        lat.set_gauge(U)
+        lat.set_clover(m0, w["c_sw"])
+        lat.tune(lq.C64, nrhs, reps=3)
+        lat.tune(lq.C128, nrhs, reps=1)
+        lats.append(lat); Us.append(U); bs.append(b); xs.append(torch.zeros_like(b)); nr.append(nrhs); m0s.append(m0)
+        units += dims[0] * dims[1] * dims[2] * dims[3] * nrhs
+    kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=w["restart"], tol=w["tol"],
+              max_restarts=args.max_restarts)
+    s = torch.cuda.current_stream()
+
+    def step():
+        for x in xs:
+            x.zero_()
+        return lq.solve_batch(lats, bs, xs, nr, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            res = step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(world)
+    t = allreduce_max(world, e0.elapsed_time(e1) * 1e-3)
+    for r in res:
+        if r.status != lq.OK or r.relres_max > w["tol"]:
+            raise SystemExit(f"batch solve did not converge: {r}")
+    # the same solves one after another (one lqcd_solve per lattice)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = []
+    for lat, b, x, n in zip(lats, bs, xs, nr):
+        x.zero_()
+        seq.append(lat.solve(b, x, n, **kw))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": world * units * args.steps / t, "unit": "site·rhs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32 inner / fp64 refinement", "data": "synthetic",
+            "config": {"workload": w["name"], "lattices": [f"{'x'.join(map(str, d[::-1]))} eps {e} m0 {m} nrhs {n}"
+                                                            for d, e, m, n in w["lattices"]]},
+            "batch": {"iterations": [r.iterations for r in res], "cycles": [r.restarts for r in res],
+                      "fp64_residuals": [r.outer_steps for r in res],
+                      "relres_max": [r.relres_max for r in res],
+                      "sequential_s": t_seq, "batch_s": t / args.steps,
+                      "speedup_vs_sequential": t_seq / (t / args.steps)},
+            "clocks": clk.summary()}
+    for lat in lats:
+        lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -645,6 +734,8 @@ def main():
         run_kernel_workload(args, w)
     elif w.get("kind") == "adjoint":
         run_adjoint_workload(args, w)
+    elif w.get("kind") == "batch":
+        run_batch_workload(args, w)
     else:
         run_gpu(args, w)
 

@@ -175,7 +175,8 @@ def test_schur_prepare_reconstruct(case, dtype):
 @pytest.mark.parametrize("dtype", [lq.C128, lq.C64])
 @pytest.mark.parametrize("nvec,nrhs,reorth", [(1, 1, True), (5, 3, True), (17, 12, False), (32, 16, True),
                                                (40, 16, True), (9, 40, True), (20, 2, True), (12, 6, True),
-                                               (33, 64, True)])
+                                               (33, 64, True), (32, 64, True), (24, 40, False), (7, 5, True),
+                                               (17, 1, True), (3, 31, True)])
 def test_orthogonalise_matches_projection(dtype, nvec, nrhs, reorth):
     """h = V^H w and w' = (1 - V V^H) w per rhs for an orthonormal basis (numpy QR)."""
     lat, *_ = setup((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0, 101)
@@ -330,7 +331,8 @@ def test_bf16_storage_operator(case, op, nrhs):
     assert relerr(d_out.cpu().numpy(), ref) < TOL[lq.C64]
 
 
-@pytest.mark.parametrize("nvec,nrhs", [(5, 3), (17, 12), (32, 16), (3, 2), (12, 6), (9, 40), (33, 64)])
+@pytest.mark.parametrize("nvec,nrhs", [(5, 3), (17, 12), (32, 16), (3, 2), (12, 6), (9, 40), (33, 64), (24, 64),
+                                       (1, 1), (23, 7)])
 def test_orthogonalise_bf16_basis(nvec, nrhs):
     """BF16-stored basis, complex64 w: h = V^H w and w' = (1 - V V^H) w with V the BF16-rounded basis."""
     lat, *_ = setup((4, 4, 4, 4), "exp", 0.3, -0.2, 1.0, 101)
