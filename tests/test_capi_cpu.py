@@ -53,5 +53,23 @@ def test_host_side_argument_errors(lib):
     assert lib.lqcd_packed_bytes(h, 7, lq.SITES_ODD, 3) == 0
     assert lib.lqcd_site_tile(h, 1) == 16 and lib.lqcd_site_tile(h, 12) == 2 and lib.lqcd_site_tile(h, 16) == 1
     assert lib.lqcd_status_string(lq.ERR_SINGULAR) == b"singular site block"
+    # force: bad sizes and null pointers are argument errors, a missing gauge field a state error
+    assert lib.lqcd_force(h, 0, buf, buf, buf, None) == lq.ERR_ARG
+    assert lib.lqcd_force(h, 2, None, buf, buf, None) == lq.ERR_ARG
+    assert lib.lqcd_force(h, 2, buf, buf, buf, None) == lq.ERR_STATE
+    # Gram-Schmidt step: basis sizes 1..64, BF16 storage needs nrhs <= 32 or even nrhs <= 64
+    hv = ctypes.c_void_p(32)
+    assert lib.lqcd_orthogonalise(h, lq.C64, lq.SITES_ODD, 4, 0, buf, buf, hv, hv, 1, None) == lq.ERR_ARG
+    assert lib.lqcd_orthogonalise(h, lq.C64, lq.SITES_ODD, 4, 65, buf, buf, hv, hv, 1, None) == lq.ERR_ARG
+    assert lib.lqcd_orthogonalise(h, lq.BF16S, lq.SITES_ODD, 33, 4, buf, buf, hv, hv, 1, None) == lq.ERR_ARG
+    assert lib.lqcd_orthogonalise(h, lq.BF16S, lq.SITES_ODD, 66, 4, buf, buf, hv, hv, 1, None) == lq.ERR_ARG
+    # batch: empty batch, a lattice listed twice
+    ctxs = (ctypes.c_void_p * 2)(h.value, h.value)
+    params = (lq.SolveParams * 2)()
+    nr = (ctypes.c_int * 2)(1, 1)
+    ptrs = (ctypes.c_void_p * 2)(16, 16)
+    assert lib.lqcd_solve_batch(0, ctxs, params, nr, ptrs, ptrs, None, None) == lq.ERR_ARG
+    assert lib.lqcd_solve_batch(2, ctxs, params, nr, ptrs, ptrs, None, None) == lq.ERR_ARG
+    assert b"twice" in lib.lqcd_last_error()
     assert lib.lqcd_free(h) == lq.OK
     assert lib.lqcd_free(None) == lq.OK

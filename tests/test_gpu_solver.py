@@ -188,3 +188,25 @@ def test_uneven_multi_lattice_batch_solve():
     assert len({r.restarts for r in res}) > 1      # uneven: the lattices retire at different rounds
     for lat in lats:
         lat.close()
+
+
+@pytest.mark.parametrize("nrhs,precision,restart_len", [(64, lq.C64, 8), (40, lq.BF16S, 12), (1, lq.BF16S, 20),
+                                                         (3, lq.C64, 64), (2, lq.C128, 1)])
+def test_solver_size_limits(nrhs, precision, restart_len):
+    """Largest rhs block (64: two rhs per lane in the streaming Gram-Schmidt kernel), BF16 with an even nrhs > 32,
+    the largest restart length (64 basis vectors: the register-tiled kernel above 32) and GMRES(1)."""
+    dims = (4, 4, 4, 4)
+    m0, c_sw = 0.3, 1.0
+    U = syn.gauge_field(dims, "exp", 0.2, seed=801)
+    b = syn.gaussian_spinors(dims, nrhs, 802)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    res = lat.solve(torch.from_numpy(b).cuda(), x, nrhs, op=lq.OP_SCHUR, precision=precision,
+                    restart_len=restart_len, tol=1e-10, max_restarts=2000)
+    torch.cuda.synchronize()
+    assert res.status == lq.OK, res
+    rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
+    assert np.all(rel <= 1e-10), rel
+    lat.close()
