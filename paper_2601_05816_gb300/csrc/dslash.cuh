@@ -220,9 +220,17 @@ __device__ __forceinline__ void hop_compute(const typename Cplx<Real>::T* u, con
   }
 }
 
+// Packed index with the rhs count fixed at compile time (NRHS > 0: a site tile of one
+// site, S = 1, which holds for nrhs >= 16): the component offsets become immediates.
+template <int NRHS>
+__device__ __forceinline__ int64_t lidx(const PackedLayout& lay, int64_t i, int c, int r) {
+  if constexpr (NRHS > 0) return (i * 12 + c) * NRHS + r;
+  else return lay.index(i, c, r);
+}
+
 // One hopping direction with direct (register) loads of the link and the neighbour
 // (BATCH: as one batch of volatile loads).
-template <typename Real, int NR, int MU, int DIR, bool BATCH, typename HIN>
+template <typename Real, int NR, int MU, int DIR, bool BATCH, typename HIN, int NRHS = 0>
 __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
                                         const HIN* hin, MC<Real, NR> acc[12]) {
   using C = typename Cplx<Real>::T;
@@ -237,16 +245,16 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = ldg_batch(lp + (int64_t)e * a.g.V);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) mc_load_batch(up[k], hin + a.lay.index(ncb, k, r0));
+    for (int k = 0; k < 6; ++k) mc_load_batch(up[k], hin + lidx<NRHS>(a.lay, ncb, k, r0));
 #pragma unroll
-    for (int k = 0; k < 6; ++k) mc_load_batch(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+    for (int k = 0; k < 6; ++k) mc_load_batch(dn[k], hin + lidx<NRHS>(a.lay, ncb, 6 + k, r0));
   } else {
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      mc_load(up[k], hin + a.lay.index(ncb, k, r0));
-      mc_load(dn[k], hin + a.lay.index(ncb, 6 + k, r0));
+      mc_load(up[k], hin + lidx<NRHS>(a.lay, ncb, k, r0));
+      mc_load(dn[k], hin + lidx<NRHS>(a.lay, ncb, 6 + k, r0));
     }
   }
   hop_compute<Real, NR, MU, DIR>(u, up, dn, acc);
@@ -315,7 +323,7 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
 }
 
 // The whole operator on one target site for this thread's NR rhs.
-template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN>
+template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0>
 __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site) {
   using C = typename Cplx<Real>::T;
   const int r0 = threadIdx.x * NR;
@@ -336,14 +344,14 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
   if (a.hop) {
     const Coord c = site_coords(a.g, p, cb);
     const HIN* hin = reinterpret_cast<const HIN*>(a.hop_in) + (a.full ? (1 - p) * a.half_elems : 0);
-    hop_dir<Real, NR, 0, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 0, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, +1, BATCH, HIN>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, -1, BATCH, HIN>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 0, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 1, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 2, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    hop_dir<Real, NR, 3, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -355,7 +363,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
     const SIN* sp = reinterpret_cast<const SIN*>(a.self_in) + base;
     MC<Real, NR> s[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) mc_load(s[k], sp + a.lay.index(cb, k, r0));
+    for (int k = 0; k < 12; ++k) mc_load(s[k], sp + lidx<NRHS>(a.lay, cb, k, r0));
     if (SELF == SELF_SCALAR) {
 #pragma unroll
       for (int k = 0; k < 12; ++k)
@@ -379,7 +387,7 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
     MC<Real, NR> t[12];
     site_block_apply<Real, NR>(a.blocks_inv, a.g.V, eo_site, acc, t);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) mc_store(op + a.lay.index(cb, k, r0), t[k]);
+    for (int k = 0; k < 12; ++k) mc_store(op + lidx<NRHS>(a.lay, cb, k, r0), t[k]);
   } else {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -387,18 +395,18 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
 #pragma unroll
         for (int q = 0; q < NR; ++q) { acc[k].re[q] *= a.post_scalar; acc[k].im[q] *= a.post_scalar; }
       }
-      mc_store(op + a.lay.index(cb, k, r0), acc[k]);
+      mc_store(op + lidx<NRHS>(a.lay, cb, k, r0), acc[k]);
     }
   }
 }
 
 template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN>
+          typename SIN, int NRHS = 0>
 __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   if (a.skip != nullptr && *a.skip != 0) return;
   if (!LOOP) {
     const int site = blockIdx.x * blockDim.y + threadIdx.y;
-    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN>(a, site);
+    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS>(a, site);
     return;
   }
   // persistent CTAs: each walks one contiguous chunk of target sites, blockDim.y
@@ -407,7 +415,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   const int s0 = blockIdx.x * a.loop_chunk;
   const int s1 = min(s0 + a.loop_chunk, a.n_target);
   for (int site = s0 + threadIdx.y; site < s1; site += blockDim.y)
-    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN>(a, site);
+    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS>(a, site);
 }
 
 // Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
@@ -419,6 +427,7 @@ struct DslashVariant {
   int stages;  // 0: direct register loads; >= 2: cp.async pipeline depth (dslash_async.cuh)
   int batch;   // direct loads: 1 = each direction's loads issued as one batch
   int loop;    // direct loads: 1 = persistent CTAs walking contiguous chunks of sites
+  int nrhs_fixed = 0;  // > 0: compiled for this rhs count only (immediate component offsets)
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -431,9 +440,9 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
 template <typename Real, int NR, int SM, int PM, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN>
+          typename SIN, int NRHS = 0>
 cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
-  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN>;
+  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS>;
   dim3 grid((a.n_target + block.y - 1) / block.y);
   if (LOOP) {
     // one wave of persistent CTAs, each with an equal contiguous chunk of sites
@@ -456,11 +465,12 @@ cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
 }
 
 template <typename Real, int NR, int MAXT, int MINB, bool BATCH, bool LOOP = false,
-          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T>
+          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
+  if (NRHS > 0 && (a.lay.nrhs != NRHS || a.lay.log_s != 0)) return cudaErrorInvalidValue;
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
-#define LQCD_DS(SM, PM) return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN>(a, block, s)
+#define LQCD_DS(SM, PM) return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS>(a, block, s)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -475,6 +485,10 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
 // (the variants compile in parallel).
 #define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB, BATCH, LOOP) \
   template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, BATCH, LOOP>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+// ... and of a variant with the rhs count fixed at compile time.
+#define LQCD_DSLASH_VARIANT_NRHS_TU(REAL, NR, MAXT, MINB, NRHS)                                            \
+  template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, false, false, typename Cplx<REAL>::T, \
+                                             typename Cplx<REAL>::T, NRHS>(const DslashArgs<REAL>&, int, int, cudaStream_t);
 
 // FP32 arithmetic on BF16-stored inputs (hop input HIN, self-term input SIN), FP32 output.
 cudaError_t launch_dslash_bf16(const DslashArgs<float>& a, int self_mode, int post_mode, bool hop_bf16,

@@ -6,7 +6,8 @@ namespace lqcd {
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
 //  batched loads, persistent chunk loop}
-const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1}};
+const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
+                             {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -23,6 +24,8 @@ extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, true>
 extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, true, true>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
@@ -38,6 +41,7 @@ DslashVariant dslash_variant(bool f64, int idx) { return f64 ? kF64[idx] : kF32[
 bool dslash_variant_ok(bool f64, int idx, int nrhs) {
   if (idx < 0 || idx >= dslash_variant_count(f64)) return false;
   const DslashVariant v = dslash_variant(f64, idx);
+  if (v.nrhs_fixed > 0 && nrhs != v.nrhs_fixed) return false;
   return nrhs % v.nr == 0 && nrhs / v.nr <= v.threads;
 }
 
@@ -65,6 +69,8 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
     case 10: return launch_dslash_variant<float, 2, 128, 4, true, true>(a, self_mode, post_mode, s);
     case 11: return launch_dslash_variant<float, 2, 256, 2, false, true>(a, self_mode, post_mode, s);
     case 12: return launch_dslash_variant<float, 1, 128, 6, false, true>(a, self_mode, post_mode, s);
+    case 13: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16>(a, self_mode, post_mode, s);
+    case 14: return launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }

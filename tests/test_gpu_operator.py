@@ -250,7 +250,7 @@ def test_every_kernel_variant_and_tuner(dtype):
     dims, kind, eps, m0, c_sw = CASES[0]
     lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
     lib = lq.load()
-    for nrhs in (4, 6):
+    for nrhs in (4, 6, 16):   # 16: also the variants compiled for 16 rhs
         psi = syn.gaussian_spinors(dims, nrhs, 500 + nrhs)
         psi_o = oracle.split_parity(psi, 1)
         ref_f = oracle.apply_D(U, psi, m0, C)

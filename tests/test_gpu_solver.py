@@ -210,3 +210,33 @@ def test_solver_size_limits(nrhs, precision, restart_len):
     rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
     assert np.all(rel <= 1e-10), rel
     lat.close()
+
+
+@pytest.fixture(scope="module")
+def bench_problem():
+    """The bench workload's inputs and the oracle's clover term (computed once)."""
+    dims = (32, 16, 16, 16)
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1000)
+    b = syn.gaussian_spinors(dims, 16, 1001)
+    return dims, U, b, oracle.clover_term(U, 1.0)
+
+
+@pytest.mark.parametrize("precision", [lq.C64, lq.BF16S])
+def test_bench_configuration_solve_sampled(precision, bench_problem):
+    """The bench's timed solve (16^3 x 32, clover, exp(i 0.3 H), m0 = -0.2, 16 rhs, odd-even GMRES(32) in FP64
+    refinement, tol 1e-10, CUDA graphs): the oracle's residual of rhs 0 and 15 of the GPU solution is <= 1e-10."""
+    dims, U, b, C = bench_problem
+    m0, c_sw, nrhs = -0.2, 1.0, 16
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    res = lat.solve(torch.from_numpy(b).cuda(), x, nrhs, op=lq.OP_SCHUR, precision=precision, restart_len=32,
+                    tol=1e-10, max_restarts=500, use_graph=True)
+    torch.cuda.synchronize()
+    assert res.status == lq.OK, res
+    xs = x.cpu().numpy()
+    lat.close()
+    for k in (0, nrhs - 1):
+        r = b[k:k + 1] - oracle.apply_D(U, xs[k:k + 1], m0, C)
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b[k]), k
