@@ -213,7 +213,12 @@ typedef struct {
                          recomputes the FP64 residual) */
   int x0_given;       /* 1: x holds the initial guess; 0: start from x = 0 */
   int use_graph;      /* 1: replay each Arnoldi cycle as a captured CUDA graph */
-  int reorth;         /* 1: CGS2 (default); 0: one classical Gram-Schmidt pass */
+  int reorth;         /* Gram-Schmidt of the Arnoldi step: 0: one classical pass (CGS1);
+                         1: CGS2, three passes over the basis per step; 2: CGS2 with the
+                         re-orthogonalisation delayed by one step, two passes per step
+                         (C64 / BF16S with restart_len <= 32 and nrhs <= 32, else as 1).
+                         A BF16 basis
+                         always re-orthogonalises (0 acts as 1) */
   int profile;        /* 1: time operator and Gram-Schmidt launches with CUDA events
                          (use_graph is then ignored) */
   int dagger;         /* 1: solve the adjoint system D^dagger x = b instead, as

@@ -283,12 +283,12 @@ class Lattice:
 
     def solve(self, b, x, nrhs: int, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
               max_restarts: int = 200, tol: float = 1e-10, inner_tol: float = 0.0, x0_given: bool = False,
-              use_graph: bool = True, reorth: bool = True, profile: bool = False, dagger: bool = False,
+              use_graph: bool = True, reorth: int = 2, profile: bool = False, dagger: bool = False,
               stream=None) -> SolveResult:
         """Batched GMRES on D x = b (dagger: D^dagger x = b); b and x complex128 canonical [nrhs][V][4][3],
         host (numpy) or device."""
         p = SolveParams(op, precision, restart_len, max_restarts, tol, inner_tol, int(x0_given), int(use_graph),
-                        int(reorth), int(profile), int(dagger))
+                        int(reorth), int(profile), int(dagger))  # reorth: 0 CGS1, 1 CGS2, 2 delayed CGS2
         its = (ctypes.c_int * nrhs)()
         rel = (ctypes.c_double * nrhs)()
         st = SolveStats()
@@ -310,7 +310,7 @@ class Lattice:
 
 def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
                 max_restarts: int = 200, tol=1e-10, inner_tol: float = 0.0, use_graph: bool = True,
-                reorth: bool = True, stream=None):
+                reorth: int = 2, stream=None):
     """Batched GMRES over several lattices of uneven size (lqcd_solve_batch); returns one SolveResult each.
 
     tol may be one value or one per lattice; b and x complex128 canonical per lattice (host or device).

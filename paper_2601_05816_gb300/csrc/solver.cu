@@ -49,9 +49,58 @@ __global__ void cycle_init_kernel(GmresState s, const double* __restrict__ beta0
   }
 }
 
-// Column j of the Hessenberg matrix from the Gram-Schmidt coefficients, the
-// stored rotations applied to it, a new rotation (c = |a|/rho, s = (a/|a|) h/rho),
-// gamma_{j+1} = -conj(s) gamma_j, gamma_j = c gamma_j, and the stop test.
+// Givens step for Hessenberg column j of rhs r: the stored rotations applied to
+// col[0..j], a new rotation (c = |a|/rho, s = (a/|a|) beta/rho) against the
+// sub-diagonal entry beta, gamma_{j+1} = -conj(s) gamma_j, gamma_j = c gamma_j,
+// and the stop test (|gamma_{j+1}| <= thr, happy breakdown beta <= 1e-14 ||column||,
+// the last column, or a non-finite value). Returns whether the cycle goes on.
+__device__ bool givens_step(const GmresState& s, int r, int j, double2* col, double beta, double w2) {
+  double* cs = s.cs + (int64_t)r * s.m;
+  double2* sn = s.sn + (int64_t)r * s.m;
+  for (int i = 0; i < j; ++i) {
+    const double2 top = col[i], bot = col[i + 1];
+    const double c = cs[i];
+    const double2 sv = sn[i];
+    // top' = c top + s bot ; bot' = -conj(s) top + c bot
+    col[i] = make_double2(c * top.x + sv.x * bot.x - sv.y * bot.y, c * top.y + sv.x * bot.y + sv.y * bot.x);
+    col[i + 1] = make_double2(-(sv.x * top.x + sv.y * top.y) + c * bot.x,
+                              -(sv.x * top.y - sv.y * top.x) + c * bot.y);
+  }
+  const double2 a = col[j];
+  const double aa = hypot(a.x, a.y);
+  const double rho = hypot(aa, beta);
+  double c;
+  double2 sv, rjj;
+  if (rho == 0.0) {
+    c = 1.0; sv = make_double2(0, 0); rjj = make_double2(0, 0);
+  } else if (aa == 0.0) {
+    c = 0.0; sv = make_double2(1, 0); rjj = make_double2(rho, 0);
+  } else {
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    c = aa / rho;
+    sv = make_double2(ph.x * beta / rho, ph.y * beta / rho);
+    rjj = make_double2(ph.x * rho, ph.y * rho);
+  }
+  cs[j] = c;
+  sn[j] = sv;
+  col[j] = rjj;
+  double2* gm = s.gamma + (int64_t)r * (s.m + 1);
+  const double2 gj = gm[j];
+  gm[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+  gm[j] = make_double2(c * gj.x, c * gj.y);
+  s.k[r] = j + 1;
+  const double res = hypot(gm[j + 1].x, gm[j + 1].y);
+  const bool bad = !(isfinite(res) && isfinite(beta));
+  const bool stop = bad || res <= s.thr[r] || beta <= 1e-14 * sqrt(w2) || j == s.m - 1;
+  if (stop) {
+    s.done[r] = 1;
+    if (bad) s.k[r] = j;  // discard the step that produced a non-finite value
+  }
+  return !stop;
+}
+
+// Column j of the Hessenberg matrix from the Gram-Schmidt coefficients (CGS1 / CGS2)
+// and the Givens step; scale = 1 / beta for the normalisation of the next vector.
 __global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h1,
                               const double2* __restrict__ h2, const double2* __restrict__ hn, int pythag) {
   const int r = threadIdx.x;
@@ -75,57 +124,157 @@ __global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h
       const double beta2 = fmax(hn[(int64_t)(j + 1) * nrhs + r].x - (pythag ? h2sq : 0.0), 0.0);
       const double beta = sqrt(beta2);
       w2 += beta2;
-      double* cs = s.cs + (int64_t)r * s.m;
-      double2* sn = s.sn + (int64_t)r * s.m;
-      for (int i = 0; i < j; ++i) {
-        const double2 top = col[i], bot = col[i + 1];
-        const double c = cs[i];
-        const double2 sv = sn[i];
-        // top' = c top + s bot ; bot' = -conj(s) top + c bot
-        col[i] = make_double2(c * top.x + sv.x * bot.x - sv.y * bot.y, c * top.y + sv.x * bot.y + sv.y * bot.x);
-        col[i + 1] = make_double2(-(sv.x * top.x + sv.y * top.y) + c * bot.x,
-                                  -(sv.x * top.y - sv.y * top.x) + c * bot.y);
-      }
-      const double2 a = col[j];
-      const double aa = hypot(a.x, a.y);
-      const double rho = hypot(aa, beta);
-      double c;
-      double2 sv, rjj;
-      if (rho == 0.0) {
-        c = 1.0; sv = make_double2(0, 0); rjj = make_double2(0, 0);
-      } else if (aa == 0.0) {
-        c = 0.0; sv = make_double2(1, 0); rjj = make_double2(rho, 0);
-      } else {
-        const double2 ph = make_double2(a.x / aa, a.y / aa);
-        c = aa / rho;
-        sv = make_double2(ph.x * beta / rho, ph.y * beta / rho);
-        rjj = make_double2(ph.x * rho, ph.y * rho);
-      }
-      cs[j] = c;
-      sn[j] = sv;
-      col[j] = rjj;
-      double2* gm = s.gamma + (int64_t)r * (s.m + 1);
-      const double2 gj = gm[j];
-      gm[j + 1] = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
-      gm[j] = make_double2(c * gj.x, c * gj.y);
-      s.k[r] = j + 1;
-      const double res = hypot(gm[j + 1].x, gm[j + 1].y);
-      const bool bad = !(isfinite(res) && isfinite(beta));
-      const bool stop = bad || res <= s.thr[r] || beta <= 1e-14 * sqrt(w2) || j == s.m - 1;
-      if (stop) {
-        s.done[r] = 1;
-        s.scale[r] = 0.0;
-        if (bad) s.k[r] = j;  // discard the step that produced a non-finite value
-      } else {
-        s.scale[r] = beta > 0.0 ? 1.0 / beta : 0.0;
-        live = true;
-      }
+      live = givens_step(s, r, j, col, beta, w2);
+      s.scale[r] = live ? (beta > 0.0 ? 1.0 / beta : 0.0) : 0.0;
     } else {
       s.scale[r] = 0.0;
     }
   }
   const int any = __syncthreads_or(live);
   if (threadIdx.x == 0) *s.all_done = any ? 0 : 1;
+}
+
+// ---------------------------------------------------------------- delayed CGS2
+//
+// Classical Gram-Schmidt with the re-orthogonalisation delayed by one step, so that
+// each Arnoldi step reads the basis twice instead of three times. At step j the basis
+// holds the final q_0 .. q_{j-1} (Q_j) and a once-orthogonalised candidate
+// q~_j = Q_j a_j + rho_j q_j (a_j, rho_j known from the previous step), and w = A q~_j:
+//   pass A: e = [Q_j, q~_j]^H w, omega = ||w||^2, and in the same pass q_j =
+//           (q~_j - Q_j a_j) / rho_j in place (the dots use the old slot);
+//   coef2:  b = e_{<j}, c = q_j^H w = (e_j - a_j^H b) / rho_j, nu^2 = omega - |b|^2 - |c|^2
+//           (Pythagoras; nu only normalises the next candidate, its error is absorbed
+//           one step later);
+//   pass B: q~_{j+1} = (w - Q_j b - q_j c) / nu, d = Q_{j+1}^H (nu q~_{j+1}), ||nu q~_{j+1}||^2;
+//   coef1:  a_{j+1} = d / nu, rho_{j+1}^2 = ||q~_{j+1}||^2 - |a_{j+1}|^2, and Hessenberg
+//           column j: A q_j = (A q~_j - A Q_j a_j) / rho_j with q~_{j+1} = Q_{j+1} a_{j+1} +
+//           rho_{j+1} q_{j+1} gives
+//           H_{l,j} = (bc_l + nu a_{j+1,l} - (H_{:,<j} a_j)_l) / rho_j (l <= j), H_{j+1,j} = nu rho_{j+1} / rho_j
+//           (bc = [b; c], H_{:,<j} the unrotated earlier columns), then its Givens step and the
+//           stop test - before the next operator apply, so finished rhs skip it.
+// One warp per rhs (a CTA of 32 nrhs threads, up to 32 rhs per warp row), lanes over the
+// basis index; sums over lanes in a fixed shuffle order.
+struct DcgsState {
+  double2* Hraw;    // [nrhs][m][m + 1] unrotated final columns
+  double2* bc;      // [nrhs][m + 1] pending [b; c]
+  double2* a_cur;   // [nrhs][m] a_j of the current candidate
+  double2* a_pend;  // [nrhs][m] a_j of the pending column
+  double* rho_cur;  // [nrhs]
+  double* rho_pend; // [nrhs]
+  double* nu_pend;  // [nrhs]
+  double2* g;       // [m + 1][nrhs] pass-B update coefficients
+  double2* acoef;   // [m][nrhs] pass-A finalisation coefficients (a_j)
+  double* scale2;   // [nrhs] 1 / rho_j
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// coef1 after pass B of step jn - 1 (dd: Q_jn^H (nu q~_jn) in slots 0 .. jn-1, the norm in slot
+// jn): a_jn, rho_jn, final column jn - 1 and its Givens step. Lane l handles basis index l
+// (the restart length is at most 32).
+__global__ void dcgs_coef1_kernel(GmresState s, DcgsState d, int jn, const double2* __restrict__ dd) {
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int nrhs = s.nrhs, m = s.m;
+  bool live = false;
+  if (r < nrhs && s.done[r]) {  // finished rhs: its next slot stays as it is (finite, unused)
+    if (lane < jn) d.acoef[(int64_t)lane * nrhs + r] = make_double2(0.0, 0.0);
+    if (lane == 0) d.scale2[r] = 1.0;
+  } else if (r < nrhs) {
+    const double nu = d.nu_pend[r], rho_p = d.rho_pend[r];
+    const double inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
+    double2* a = d.a_cur + (int64_t)r * m;
+    const double2* ap = d.a_pend + (int64_t)r * m;
+    double2 al = make_double2(0.0, 0.0);
+    if (lane < jn) {
+      al = dd[(int64_t)lane * nrhs + r];
+      al.x *= inv_nu;
+      al.y *= inv_nu;
+      a[lane] = al;
+    }
+    const double asq = warp_sum(al.x * al.x + al.y * al.y);
+    const double alpha = dd[(int64_t)jn * nrhs + r].x * inv_nu * inv_nu;
+    const double rho = sqrt(fmax(alpha - asq, 0.0));
+    // column j = jn - 1, row l = lane
+    const int j = jn - 1;
+    const double2* bc = d.bc + (int64_t)r * (m + 1);
+    double2* raw = d.Hraw + ((int64_t)r * m + j) * (m + 1);
+    double2 v = make_double2(0.0, 0.0);
+    if (lane <= j) {
+      v = make_double2(bc[lane].x + nu * al.x, bc[lane].y + nu * al.y);
+      for (int k = (lane > 0 ? lane - 1 : 0); k < j; ++k) {  // column k has rows 0 .. k + 1
+        const double2 h = d.Hraw[((int64_t)r * m + k) * (m + 1) + lane], ak = ap[k];
+        v.x -= h.x * ak.x - h.y * ak.y;
+        v.y -= h.x * ak.y + h.y * ak.x;
+      }
+      v.x /= rho_p;
+      v.y /= rho_p;
+      raw[lane] = v;
+    }
+    const double beta = nu * rho / rho_p;
+    const double w2 = warp_sum(v.x * v.x + v.y * v.y) + beta * beta;
+    __syncwarp();
+    int go = 0;
+    if (lane == 0) {
+      raw[j + 1] = make_double2(beta, 0.0);
+      double2* col = s.H + ((int64_t)r * m + j) * (m + 1);
+      for (int l = 0; l <= j; ++l) col[l] = raw[l];
+      go = givens_step(s, r, j, col, beta, w2) && rho > 0.0 && isfinite(rho);
+      if (!go) s.done[r] = 1;
+      d.rho_cur[r] = rho;
+      d.scale2[r] = go ? 1.0 / rho : 1.0;
+    }
+    go = __shfl_sync(0xffffffffu, go, 0);
+    if (lane < jn) d.acoef[(int64_t)lane * nrhs + r] = go ? al : make_double2(0.0, 0.0);
+    live = go != 0;
+  }
+  const int any = __syncthreads_or(live && lane == 0);
+  if (threadIdx.x == 0) *s.all_done = any ? 0 : 1;
+}
+
+// coef2 after pass A of step j (e: [Q_j, q~_j]^H w in slots 0 .. j, ||w||^2 in slot j + 1):
+// c, nu, the pass-B coefficients g = [b; c] and the pending column.
+__global__ void dcgs_coef2_kernel(GmresState s, DcgsState d, int j, const double2* __restrict__ e) {
+  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int nrhs = s.nrhs, m = s.m;
+  if (r >= nrhs) return;
+  if (s.done[r]) {  // finished rhs: next candidate 0
+    if (lane <= j) d.g[(int64_t)lane * nrhs + r] = make_double2(0.0, 0.0);
+    if (lane == 0) s.scale[r] = 0.0;
+    return;
+  }
+  const double rho = j == 0 ? 1.0 : d.rho_cur[r];
+  const double2* a = d.a_cur + (int64_t)r * m;
+  double2 bl = make_double2(0.0, 0.0), aa = make_double2(0.0, 0.0);
+  if (lane < j) {
+    bl = e[(int64_t)lane * nrhs + r];
+    aa = a[lane];
+  }
+  const double abx = warp_sum(aa.x * bl.x + aa.y * bl.y), aby = warp_sum(aa.x * bl.y - aa.y * bl.x);
+  const double bsq = warp_sum(bl.x * bl.x + bl.y * bl.y);
+  const double2 ej = e[(int64_t)j * nrhs + r];
+  const double2 c = make_double2((ej.x - abx) / rho, (ej.y - aby) / rho);
+  const double omega = e[(int64_t)(j + 1) * nrhs + r].x;
+  const double nu = sqrt(fmax(omega - bsq - (c.x * c.x + c.y * c.y), 1e-12 * omega));
+  double2* bc = d.bc + (int64_t)r * (m + 1);
+  double2* ap = d.a_pend + (int64_t)r * m;
+  if (lane < j) {
+    bc[lane] = bl;
+    ap[lane] = aa;
+    d.g[(int64_t)lane * nrhs + r] = bl;
+  }
+  if (lane == 0) {
+    bc[j] = c;
+    d.g[(int64_t)j * nrhs + r] = c;
+    d.nu_pend[r] = nu;
+    d.rho_pend[r] = rho;
+    const bool ok = isfinite(nu) && nu > 0.0;
+    s.scale[r] = ok ? 1.0 / nu : 0.0;
+    if (!ok) s.done[r] = 1;
+  }
 }
 
 // Back substitution R y = gamma per rhs; y stored [m][nrhs]; kmax = max_r k_r.
@@ -180,6 +329,16 @@ cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void
                                                          (const double2*)hn, pythag ? 1 : 0);
   return cudaGetLastError();
 }
+static cudaError_t launch_dcgs_coef1(const GmresState& s, const DcgsState& d, int jn, const void* dd,
+                                     cudaStream_t stream) {
+  dcgs_coef1_kernel<<<1, 32 * s.nrhs, 0, stream>>>(s, d, jn, (const double2*)dd);
+  return cudaGetLastError();
+}
+static cudaError_t launch_dcgs_coef2(const GmresState& s, const DcgsState& d, int j, const void* e,
+                                     cudaStream_t stream) {
+  dcgs_coef2_kernel<<<1, 32 * s.nrhs, 0, stream>>>(s, d, j, (const double2*)e);
+  return cudaGetLastError();
+}
 cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream) {
   backsub_kernel<<<1, round_threads(s.nrhs), 0, stream>>>(s);
   return cudaGetLastError();
@@ -203,6 +362,8 @@ struct SolveBufs {
   void* hn;
   GmresState st;
   BlasPlan plan;
+  int ortho;            // 0: CGS1, 1: CGS2 (three passes), 2: delayed CGS2 (two passes)
+  DcgsState dc;         // ortho == 2
 };
 
 // Gram-Schmidt of w = basis[j+1] against basis[0..j], the Givens step, and the
@@ -219,6 +380,21 @@ static lqcd_status arnoldi_ortho(const SolveBufs& b, int j, bool reorth, cudaEve
   void* w = b.bf16 ? b.w32 : next;
   const int64_t vstride = b.n_sys;
   const int* skip = b.st.all_done;
+  if (b.ortho == 2) {
+    // delayed CGS2: pass A (dots + norm of w, q_j finalised in place), coefficients, pass B
+    // (the next candidate, its dots and norm), then the final column j and its Givens step
+    LQCD_CUDA(launch_gs_pass(false, b.plan, b.n_sys, nvec, b.basis, vstride, w, nullptr, false, true, true,
+                             b.partials, b.h1, skip, s, nullptr, b.bf16, nullptr,
+                             j > 0 ? (const void*)b.dc.acoef : nullptr, b.dc.scale2),
+              "dcgs pass A");
+    LQCD_CUDA(launch_dcgs_coef2(b.st, b.dc, j, b.h1, s), "dcgs coefficients");
+    LQCD_CUDA(launch_gs_pass(false, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.dc.g, true, true, true,
+                             b.partials, b.h2, skip, s, b.st.scale, b.bf16, b.bf16 ? next : nullptr),
+              "dcgs pass B");
+    LQCD_CUDA(launch_dcgs_coef1(b.st, b.dc, j + 1, b.h2, s), "dcgs column");
+    if (ev_gs_end) LQCD_CUDA(cudaEventRecord(ev_gs_end, s), "event");
+    return LQCD_OK;
+  }
   LQCD_CUDA(launch_gs_pass(b.f64_inner, b.plan, b.n_sys, nvec, b.basis, vstride, w, nullptr, false, true,
                            false, b.partials, b.h1, skip, s, nullptr, b.bf16),
             "gs dots");
@@ -271,14 +447,15 @@ static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int 
 // elements: the dot pass reads nvec + 1 vectors; each update pass reads nvec + 1
 // and writes 1 (CGS2: two updates, the second one normalising; CGS1: one update
 // and a separate normalisation that reads and writes w once more).
-static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, bool reorth, bool bf16 = false) {
-  if (bf16) {  // BF16 basis (4 bytes per complex), FP32 w; the last pass writes the BF16 basis vector
-    const double vb = (double)n * 4.0, vw = (double)n * 8.0;
+static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, int ortho, bool bf16 = false) {
+  const double vb = (double)n * (bf16 ? 4.0 : (f64 ? 16.0 : 8.0));  // a basis vector
+  const double vw = (double)n * (f64 ? 16.0 : 8.0);                  // w (FP32 for a BF16 basis)
+  if (ortho == 2)  // delayed CGS2: two reads of the basis and w; writes the candidate and, from step 1, q_j
+    return 2 * (nvec * vb + vw) + vb + (nvec > 1 ? vb : 0.0);
+  if (bf16)  // CGS2 with a BF16 basis; the last pass writes the BF16 basis vector
     return (nvec * vb + vw) + (nvec * vb + 2 * vw) + (nvec * vb + vw + vb);
-  }
-  const double v = (double)n * (f64 ? 16.0 : 8.0);
-  const double dots = (nvec + 1) * v, upd = (nvec + 2) * v;
-  return reorth ? dots + 2 * upd : dots + upd + 2 * v;
+  const double dots = (nvec + 1) * vw, upd = (nvec + 2) * vw;
+  return ortho == 1 ? dots + 2 * upd : dots + upd + 2 * vw;
 }
 
 static lqcd_status run_cycle_direct(lqcd_ctx ctx, const SolveBufs& b, int op, bool reorth, Profile* prof,
@@ -308,8 +485,8 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
   // profiled cycle is launched kernel by kernel.
   if (!use_graph || prof->on) return run_cycle_direct(ctx, b, op, reorth, prof, s);
   char key[256];
-  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%d/%p/%p/%p/%p/%lld", op, (int)b.f64_inner, (int)b.bf16, b.nrhs, b.m,
-           (int)reorth, b.basis, b.w32, b.partials, (void*)b.st.H, (long long)b.n_sys);
+  snprintf(key, sizeof(key), "%d/%d/%d/%d/%d/%d/%d/%p/%p/%p/%p/%p/%lld", op, (int)b.f64_inner, (int)b.bf16, b.nrhs, b.m,
+           (int)reorth, b.ortho, b.basis, b.w32, b.partials, (void*)b.st.H, (void*)b.dc.g, (long long)b.n_sys);
   if (ctx->cycle.exec == nullptr || ctx->cycle.key != key) {
     if (ctx->cycle.exec) {
       cudaGraphExecDestroy(ctx->cycle.exec);
@@ -345,7 +522,7 @@ static lqcd_status run_cycle(lqcd_ctx ctx, const SolveBufs& b, int op, bool reor
 
 // Accumulate the event times of the steps that ran (j < kmax: later steps were
 // skipped on the device once every rhs had finished its cycle).
-static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n, bool f64, bool reorth, bool bf16) {
+static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n, bool f64, int ortho, bool bf16) {
   if (!prof->on) return;
   for (int j = 0; j < prof->used && j < kmax; ++j) {
     float a = 0.f, c = 0.f;
@@ -357,7 +534,7 @@ static void collect_profile(Profile* prof, int kmax, double op_bytes, int64_t n,
     if (cudaEventElapsedTime(&c, prof->ev[4 * j + 2], prof->ev[4 * j + 3]) == cudaSuccess) {
       prof->gs_ms += c;
       prof->gs_n += 1;
-      prof->gs_bytes += gs_algorithmic_bytes(n, j + 1, f64, reorth, bf16);
+      prof->gs_bytes += gs_algorithmic_bytes(n, j + 1, f64, ortho, bf16);
     }
   }
   prof->used = 0;
@@ -456,6 +633,7 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   bf16 = P.precision == LQCD_BF16S;
   m = P.restart_len;
   reorth = P.reorth != 0 || bf16;
+  const int ortho_req = P.reorth == 0 ? (bf16 ? 1 : 0) : (P.reorth == 2 ? 2 : 1);
   inner_tol = P.inner_tol > 0.0 ? P.inner_tol : (f64_inner ? 0.0 : 1e-4);
   n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
   n_half = n_full / 2;
@@ -505,6 +683,37 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   inner_done.assign(nrhs, 1);
   B.plan = blas_plan(n_sys, nrhs, ctx->num_sms);
   B.plan.wait_flag = wait_flag(ctx);
+  // delayed CGS2 needs the streaming Gram-Schmidt kernel for every basis size (FP32 or
+  // BF16 basis, restart length <= 32) and one warp per rhs (nrhs <= 32); otherwise CGS2
+  B.ortho = ortho_req;
+  if (B.ortho == 2 && (f64_inner || m > 32 || nrhs > 32 ||
+                       !(bf16 ? gs_stream_fin_supported_bf16(B.plan, n_sys, m) : gs_stream_fin_supported_f32(B.plan, n_sys, m))))
+    B.ortho = 1;
+  memset(&B.dc, 0, sizeof(B.dc));
+  if (B.ortho == 2) {
+    const size_t dpiece[10] = {sizeof(double2) * (size_t)nrhs * m * (m + 1), sizeof(double2) * (size_t)nrhs * (m + 1),
+                               sizeof(double2) * (size_t)nrhs * m, sizeof(double2) * (size_t)nrhs * m,
+                               sizeof(double) * nrhs, sizeof(double) * nrhs, sizeof(double) * nrhs,
+                               sizeof(double2) * (size_t)(m + 1) * nrhs, sizeof(double2) * (size_t)m * nrhs,
+                               sizeof(double) * nrhs};
+    size_t dbytes = 0;
+    for (size_t q : dpiece) dbytes += (q + 255) & ~(size_t)255;
+    void* dmem;
+    if ((st = workspace(ctx, "solve_dcgs", dbytes, &dmem)) != LQCD_OK) return st;
+    char* p = (char*)dmem;
+    int next = 0;
+    auto take = [&]() { void* q = p; p += (dpiece[next++] + 255) & ~(size_t)255; return q; };
+    B.dc.Hraw = (double2*)take();
+    B.dc.bc = (double2*)take();
+    B.dc.a_cur = (double2*)take();
+    B.dc.a_pend = (double2*)take();
+    B.dc.rho_cur = (double*)take();
+    B.dc.rho_pend = (double*)take();
+    B.dc.nu_pend = (double*)take();
+    B.dc.g = (double2*)take();
+    B.dc.acoef = (double2*)take();
+    B.dc.scale2 = (double*)take();
+  }
   const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
   if ((st = workspace(ctx, "solve_partials", hb * B.plan.blocks, &B.partials)) != LQCD_OK) return st;
   if ((st = workspace(ctx, "solve_h1", hb, &B.h1)) != LQCD_OK) return st;
@@ -632,7 +841,7 @@ lqcd_status SolveJob::decide(bool* run) {
       iters[r] += hs->kcycle[r];
       kmax = std::max(kmax, hs->kcycle[r]);
     }
-    collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, reorth, bf16);
+    collect_profile(&prof, kmax, op_bytes_inner, n_sys, f64_inner, B.ortho, bf16);
   }
   pending_k = false;
   if (hs->wait_err != 0)
