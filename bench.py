@@ -63,11 +63,11 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) per CGS2 step of the timed solve, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of a full 32-step Arnoldi cycle, i.e.
-# 96 streaming Gram-Schmidt launches, of the default workload; the summary is
-# profiles/gs_stream_cgs2_c64_16x16x16x32_nrhs16.md. Workloads not captured report null.
-GS_TRAFFIC_PER_STEP = {("solve", "c64"): 5.36e9}
+# DRAM bytes (read + write) per Gram-Schmidt step of the timed solve, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the streaming Gram-Schmidt launches of
+# a full 32-step Arnoldi cycle of the default workload, keyed by (workload, precision,
+# Gram-Schmidt variant); the summaries are under profiles/. Cases not captured report null.
+GS_TRAFFIC_PER_STEP = {("solve", "c64", 1): 5.36e9}
 
 
 def measured_peaks():
@@ -573,9 +573,12 @@ def run_gpu(args, w):
     op_ms = sum(r.op_ms for r in results)
     gs_ms = sum(r.ortho_ms for r in results)
     if gs_ms >= op_ms:
-        dom = dict(kernel="gs_pass (CGS2 step: 3 fused passes)", ms=gs_ms, n=sum(r.ortho_launches for r in results),
+        ortho = results[0].ortho
+        dom = dict(kernel={2: "gs_pass (delayed CGS2 step: 2 streaming passes + coefficient kernels)",
+                           1: "gs_pass (CGS2 step: 3 fused passes)"}.get(ortho, "gs_pass (CGS1 step)"),
+                   ms=gs_ms, n=sum(r.ortho_launches for r in results),
                    bytes=sum(r.ortho_bytes for r in results),
-                   traffic=GS_TRAFFIC_PER_STEP.get((args.workload, args.precision))
+                   traffic=GS_TRAFFIC_PER_STEP.get((args.workload, args.precision, ortho))
                    if "m0_prescribed" not in w else None)
     else:
         dom = dict(kernel="dslash (Schur apply: passes A + B)", ms=op_ms, n=sum(r.op_launches for r in results),

@@ -216,7 +216,9 @@ typedef struct {
   int reorth;         /* Gram-Schmidt of the Arnoldi step: 0: one classical pass (CGS1);
                          1: CGS2, three passes over the basis per step; 2: CGS2 with the
                          re-orthogonalisation delayed by one step, two passes per step
-                         (C64 / BF16S with restart_len <= 32 and nrhs <= 32, else as 1).
+                         (C64 / BF16S with restart_len <= 32 where the streaming
+                         Gram-Schmidt kernel takes the block: nrhs <= 32, or even
+                         nrhs <= 64 with C64; else as 1).
                          A BF16 basis
                          always re-orthogonalises (0 acts as 1) */
   int profile;        /* 1: time operator and Gram-Schmidt launches with CUDA events
@@ -243,6 +245,7 @@ typedef struct {
   int* iters_per_rhs;
   double* relres_per_rhs;
   int outer_steps;       /* FP64 true-residual evaluations r = b - D x (the first included) */
+  int ortho;             /* Gram-Schmidt that ran (the reorth meaning: 0, 1 or 2) */
 } lqcd_solve_stats;
 
 /* Batched restarted GMRES (Algorithm 2), each rhs independent, optionally on the

@@ -49,7 +49,7 @@ class SolveStats(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong),
         ("iters_per_rhs", ctypes.POINTER(ctypes.c_int)),
         ("relres_per_rhs", ctypes.POINTER(ctypes.c_double)),
-        ("outer_steps", ctypes.c_int),
+        ("outer_steps", ctypes.c_int), ("ortho", ctypes.c_int),
     ]
 
 
@@ -152,6 +152,7 @@ class SolveResult:
     iters_per_rhs: list
     relres_per_rhs: list
     outer_steps: int = 0
+    ortho: int = -1      # Gram-Schmidt that ran: 0 CGS1, 1 CGS2, 2 delayed CGS2
 
 
 class Lattice:
@@ -298,7 +299,7 @@ class Lattice:
                                              ctypes.byref(st), _stream(stream)), "lqcd_solve")
         return SolveResult(status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                            st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
-                           st.kernel_launches, list(its), list(rel), st.outer_steps)
+                           st.kernel_launches, list(its), list(rel), st.outer_steps, st.ortho)
 
 
     def force(self, nrhs: int, x, lam, grad_U, stream=None) -> None:
@@ -336,7 +337,8 @@ def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = 
         st = stats[i]
         out.append(SolveResult(st.status, st.restarts, st.iterations, st.seconds, st.relres_max, st.op_ms,
                                st.op_launches, st.op_bytes, st.ortho_ms, st.ortho_launches, st.ortho_bytes,
-                               st.kernel_launches, list(per_its[i]), list(per_rel[i]), st.outer_steps))
+                               st.kernel_launches, list(per_its[i]), list(per_rel[i]), st.outer_steps,
+                               st.ortho))
     return out
 
 

@@ -494,23 +494,21 @@ static void gs_dispatch(const BlasPlan& p, int64_t n, int nvec, const void* basi
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
-                           cudaStream_t stream, const double* oscale, bool basis_bf16, void* wout,
-                           const void* coef2, const double* oscale2) {
+                           cudaStream_t stream, const double* oscale, bool basis_bf16, void* wout) {
   if (nvec < 1 || nvec > 64) return cudaErrorInvalidValue;
   if (basis_bf16 && (f64 || !plan.split)) return cudaErrorInvalidValue;
-  if (coef2 != nullptr && (f64 || update || !dots || !norm)) return cudaErrorNotSupported;
   if (!f64) {
     int used = 0;
     const cudaError_t e =
         basis_bf16 ? launch_gs_stream_bf16(plan, n, nvec, basis, vstride, w, coef, update, dots, norm, partials,
-                                           skip, stream, oscale, wout, &used, coef2, oscale2)
+                                           skip, stream, oscale, wout, &used)
                    : launch_gs_stream_f32(plan, n, nvec, basis, vstride, w, coef, update, dots, norm, partials,
-                                          skip, stream, oscale, wout, &used, coef2, oscale2);
+                                          skip, stream, oscale, wout, &used);
     if (e == cudaSuccess) {
       if (!dots && !norm) return cudaSuccess;
       return launch_reduce(used, (nvec + 1) * plan.nrhs, partials, out, skip, stream);
     }
-    if (e != cudaErrorNotSupported || coef2 != nullptr) return e;
+    if (e != cudaErrorNotSupported) return e;
   }
   // FP64 runs the split kernel with one element per lane, so only for nrhs <= 32
   if (plan.split && (!f64 || plan.nrhs <= 32)) {

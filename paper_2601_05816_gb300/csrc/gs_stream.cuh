@@ -43,11 +43,6 @@ struct Args {
   const double2* coef;
   const double* oscale;
   void* wout;
-  // FIN (with DOTS, in the dot pass of the delayed re-orthogonalisation): the last basis
-  // vector v_{nvec-1} is replaced in place by (v_{nvec-1} - sum_{i < nvec-1} coef2_i v_i) * oscale2
-  const double2* coef2;
-  const double* oscale2;
-  uint32_t coef2_off;
   double2* partials;
   const int* skip;
   int* err;            // set (bit 0) if a pipeline wait gave up
@@ -155,7 +150,7 @@ __host__ __device__ constexpr bool two_ctas(int nv, int epl) { return nv * epl <
 
 // NV: the largest nvec of the instance (8, 16, 24 or 32): the dot accumulators
 // a_i live in registers, NV * EPL complex per thread.
-template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM, bool FIN = false>
+template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM>
 __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream_kernel(const Args a) {
   using C = float2;
   if (a.skip != nullptr && *a.skip != 0) return;
@@ -187,26 +182,19 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
     *abort_flag = 0;
     fence_proxy_async();  // the initialised barriers are seen by the copy engine
   }
-  C* cs2 = reinterpret_cast<C*>(smem + a.coef2_off);         // [nvec - 1][nrhs] (FIN)
   if (UPDATE)
     for (int t = tid; t < nvec * nrhs; t += kThreads) {
       const double2 c = a.coef[t];
       cs[t] = make_float2((float)c.x, (float)c.y);
     }
-  if (FIN)
-    for (int t = tid; t < (nvec - 1) * nrhs; t += kThreads) {
-      const double2 c = a.coef2[t];
-      cs2[t] = make_float2((float)c.x, (float)c.y);
-    }
   __syncthreads();
 
   float ar[NV][EPL], ai[NV][EPL];
-  float nn[EPL], sc[EPL], sc2[EPL];
+  float nn[EPL], sc[EPL];
 #pragma unroll
   for (int q = 0; q < EPL; ++q) {
     nn[q] = 0.f;
     sc[q] = (UPDATE && a.oscale != nullptr && lane_on && warp < kConsumers) ? (float)a.oscale[r + q] : 1.f;
-    sc2[q] = (FIN && lane_on && warp < kConsumers) ? (float)a.oscale2[r + q] : 1.f;
 #pragma unroll
     for (int i = 0; i < NV; ++i) { ar[i][q] = 0.f; ai[i][q] = 0.f; }
   }
@@ -301,11 +289,6 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
           for (int q = 0; q < EPL; ++q) nn[q] += wn[q].x * wn[q].x + wn[q].y * wn[q].y;
         }
         if (DOTS) {
-          // FIN: the same loads also form sum_{i < nvec-1} coef2_i v_i for the finalised last vector
-          float fr[EPL], fi[EPL];
-          C vlast[EPL];
-#pragma unroll
-          for (int q = 0; q < EPL; ++q) { fr[q] = 0.f; fi[q] = 0.f; vlast[q] = make_float2(0.f, 0.f); }
 #pragma unroll
           for (int i = 0; i < NV; ++i) {
             if (i < nvec) {
@@ -315,24 +298,8 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               for (int q = 0; q < EPL; ++q) {
                 ar[i][q] += v[q].x * wn[q].x + v[q].y * wn[q].y;
                 ai[i][q] += v[q].x * wn[q].y - v[q].y * wn[q].x;
-                if (FIN) {
-                  if (i + 1 < nvec) {
-                    const C c2 = cs2[i * nrhs + r + q];
-                    fr[q] += c2.x * v[q].x - c2.y * v[q].y;
-                    fi[q] += c2.x * v[q].y + c2.y * v[q].x;
-                  } else {
-                    vlast[q] = v[q];
-                  }
-                }
               }
             }
-          }
-          if (FIN) {  // the finalised last basis vector, in place (the dots used its old value)
-            C fv[EPL];
-#pragma unroll
-            for (int q = 0; q < EPL; ++q)
-              fv[q] = make_float2((vlast[q].x - fr[q]) * sc2[q], (vlast[q].y - fi[q]) * sc2[q]);
-            stg<EPL>((B*)basis + (int64_t)(nvec - 1) * a.vstride + row0 * nrhs + e, fv);
           }
         }
       }
@@ -394,12 +361,12 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
 struct Plan {
   bool ok = false;
   int J = 1, S = 2, TR = 4, lpr = 1, H = 1, ctas_per_sm = 1, red_vecs = 1;
-  uint32_t vt_bytes = 0, stage_bytes = 0, coef_off = 0, stage_off = 0, coef2_off = 0;
+  uint32_t vt_bytes = 0, stage_bytes = 0, coef_off = 0, stage_off = 0;
   size_t smem = 0;
 };
 
 // nv: the instance's vector capacity (8, 16, 24 or 32)
-inline Plan make_plan(int nrhs, int nvec, int nv, int epl, int elem_bytes, bool update, bool fin = false) {
+inline Plan make_plan(int nrhs, int nvec, int nv, int epl, int elem_bytes, bool update) {
   Plan p;
   if (nrhs % epl != 0 || nrhs / epl > 32 || nvec < 1 || nvec > nv) return p;
   p.lpr = nrhs / epl;
@@ -412,9 +379,7 @@ inline Plan make_plan(int nrhs, int nvec, int nv, int epl, int elem_bytes, bool 
   const size_t budget = two ? 112 * 1024 : 225 * 1024;
   p.coef_off = 128;
   const size_t coef_bytes = update ? ((size_t)nvec * nrhs * sizeof(float2) + 127) / 128 * 128 : 0;
-  const size_t coef2_bytes = fin ? ((size_t)nvec * nrhs * sizeof(float2) + 127) / 128 * 128 : 0;
-  p.coef2_off = (uint32_t)(128 + coef_bytes);
-  p.stage_off = (uint32_t)(128 + coef_bytes + coef2_bytes);
+  p.stage_off = (uint32_t)(128 + coef_bytes);
   auto stage_of = [&](int J, uint32_t* vt) {
     const size_t TR = (size_t)unit * J;
     *vt = (uint32_t)(TR * nrhs * elem_bytes);

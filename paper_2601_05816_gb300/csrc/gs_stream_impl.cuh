@@ -6,9 +6,9 @@
 namespace lqcd {
 namespace gss {
 
-template <typename B, int EPL, int NV, bool U, bool D, bool N, bool F = false>
+template <typename B, int EPL, int NV, bool U, bool D, bool N>
 static cudaError_t launch_one(const Plan& p, int blocks, const Args& a, cudaStream_t s) {
-  auto k = gs_stream_kernel<B, EPL, NV, U, D, N, F>;
+  auto k = gs_stream_kernel<B, EPL, NV, U, D, N>;
   // allow the largest layout make_plan can choose, once per device
   static unsigned configured = 0;
   int dev = 0;
@@ -27,12 +27,8 @@ static cudaError_t launch_one(const Plan& p, int blocks, const Args& a, cudaStre
 }
 
 template <typename B, int EPL, int NV>
-static cudaError_t launch_flags(bool up, bool dots, bool norm, bool fin, const Plan& p, int blocks, const Args& a,
+static cudaError_t launch_flags(bool up, bool dots, bool norm, const Plan& p, int blocks, const Args& a,
                                 cudaStream_t s) {
-  if (fin) {
-    if (!up && dots && norm) return launch_one<B, EPL, NV, false, true, true, true>(p, blocks, a, s);
-    return cudaErrorNotSupported;
-  }
   if (up && dots && norm) return launch_one<B, EPL, NV, true, true, true>(p, blocks, a, s);
   if (!up && dots && norm) return launch_one<B, EPL, NV, false, true, true>(p, blocks, a, s);
   if (up && dots) return launch_one<B, EPL, NV, true, true, false>(p, blocks, a, s);
@@ -46,9 +42,8 @@ template <typename B>
 static cudaError_t launch_stream(const BlasPlan& plan, int64_t n, int nvec, const void* basis, int64_t vstride,
                                  void* w, const void* coef, bool update, bool dots, bool norm, void* partials,
                                  const int* skip, cudaStream_t stream, const double* oscale, void* wout,
-                                 int* blocks_used, const void* coef2, const double* oscale2) {
+                                 int* blocks_used) {
   const int nrhs = plan.nrhs;
-  const bool fin = coef2 != nullptr;
   const int epl = nrhs <= 32 ? 1 : 2;
   if (plan.wait_flag == nullptr || nrhs > 64 || (nrhs > 32 && nrhs % 2 != 0) || n % nrhs != 0)
     return cudaErrorNotSupported;
@@ -59,7 +54,7 @@ static cudaError_t launch_stream(const BlasPlan& plan, int64_t n, int nvec, cons
     return cudaErrorNotSupported;
   if (nvec > 32) return cudaErrorNotSupported;
   const int nv = nvec <= 8 ? 8 : (nvec <= 16 ? 16 : (nvec <= 24 ? 24 : 32));
-  const Plan p = make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), update, fin);
+  const Plan p = make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), update);
   if (!p.ok) return cudaErrorNotSupported;
   Args a;
   a.Q = n / nrhs;
@@ -76,9 +71,6 @@ static cudaError_t launch_stream(const BlasPlan& plan, int64_t n, int nvec, cons
   a.stage_bytes = p.stage_bytes;
   a.coef_off = p.coef_off;
   a.stage_off = p.stage_off;
-  a.coef2_off = p.coef2_off;
-  a.coef2 = (const double2*)coef2;
-  a.oscale2 = oscale2;
   a.basis = basis;
   a.w = w;
   a.coef = (const double2*)coef;
@@ -94,10 +86,10 @@ static cudaError_t launch_stream(const BlasPlan& plan, int64_t n, int nvec, cons
   if (blocks < 1) blocks = 1;
   *blocks_used = (int)blocks;
 #define GSS_NV(E)                                                                                   \
-  if (nv == 8) return launch_flags<B, E, 8>(update, dots, norm, fin, p, (int)blocks, a, stream);         \
-  if (nv == 16) return launch_flags<B, E, 16>(update, dots, norm, fin, p, (int)blocks, a, stream);       \
-  if (nv == 24) return launch_flags<B, E, 24>(update, dots, norm, fin, p, (int)blocks, a, stream);       \
-  return launch_flags<B, E, 32>(update, dots, norm, fin, p, (int)blocks, a, stream);
+  if (nv == 8) return launch_flags<B, E, 8>(update, dots, norm, p, (int)blocks, a, stream);         \
+  if (nv == 16) return launch_flags<B, E, 16>(update, dots, norm, p, (int)blocks, a, stream);       \
+  if (nv == 24) return launch_flags<B, E, 24>(update, dots, norm, p, (int)blocks, a, stream);       \
+  return launch_flags<B, E, 32>(update, dots, norm, p, (int)blocks, a, stream);
   if (epl == 1) {
     GSS_NV(1)
   } else {
@@ -106,18 +98,18 @@ static cudaError_t launch_stream(const BlasPlan& plan, int64_t n, int nvec, cons
 #undef GSS_NV
 }
 
-// Whether launch_stream can run the finalising pass (and the other passes) for every
-// basis size up to nvec_max on this plan and vector length.
+// Whether launch_stream runs the dot + norm pass and the update + dot + norm pass for
+// every basis size up to nvec_max on this plan and vector length.
 template <typename B>
-static bool fin_supported(const BlasPlan& plan, int64_t n, int nvec_max) {
+static bool passes_supported(const BlasPlan& plan, int64_t n, int nvec_max) {
   const int nrhs = plan.nrhs;
   if (plan.wait_flag == nullptr || nrhs > 64 || (nrhs > 32 && nrhs % 2 != 0) || n % nrhs != 0) return false;
   if (((n * (int64_t)sizeof(B)) & 15) || nvec_max > 32 || nvec_max < 1) return false;
   const int epl = nrhs <= 32 ? 1 : 2;
   for (int nvec = 1; nvec <= nvec_max; ++nvec) {
     const int nv = nvec <= 8 ? 8 : (nvec <= 16 ? 16 : (nvec <= 24 ? 24 : 32));
-    if (!make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), false, true).ok) return false;
-    if (!make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), true, false).ok) return false;
+    if (!make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), false).ok) return false;
+    if (!make_plan(nrhs, nvec, nv, epl, (int)sizeof(B), true).ok) return false;
   }
   return true;
 }

@@ -42,21 +42,18 @@ BlasPlan blas_plan(int64_t n, int nrhs, int num_sms);
 // bulk asynchronous copies (FP32 or BF16 basis, nrhs <= 32 or even nrhs <= 64).
 // Returns cudaErrorNotSupported (launching nothing) when no layout fits; on success
 // the per-CTA partials of *blocks_used CTAs are written.
-// coef2 / oscale2 (optional): the finalising pass of the delayed re-orthogonalisation,
-// see launch_gs_pass.
 cudaError_t launch_gs_stream_f32(const BlasPlan& plan, int64_t n, int nvec, const void* basis, int64_t vstride,
                                  void* w, const void* coef, bool update, bool dots, bool norm, void* partials,
                                  const int* skip, cudaStream_t stream, const double* oscale, void* wout,
-                                 int* blocks_used, const void* coef2 = nullptr, const double* oscale2 = nullptr);
+                                 int* blocks_used);
 cudaError_t launch_gs_stream_bf16(const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                                   int64_t vstride, void* w, const void* coef, bool update, bool dots, bool norm,
                                   void* partials, const int* skip, cudaStream_t stream, const double* oscale,
-                                  void* wout, int* blocks_used, const void* coef2 = nullptr,
-                                  const double* oscale2 = nullptr);
-// Whether the streaming kernel runs every pass of the delayed re-orthogonalisation for
-// basis sizes 1 .. nvec_max (FP32 or BF16 basis).
-bool gs_stream_fin_supported_f32(const BlasPlan& plan, int64_t n, int nvec_max);
-bool gs_stream_fin_supported_bf16(const BlasPlan& plan, int64_t n, int nvec_max);
+                                  void* wout, int* blocks_used);
+// Whether the streaming kernel runs the passes of the delayed re-orthogonalisation (dots +
+// norm; update + dots + norm) for basis sizes 1 .. nvec_max (FP32 or BF16 basis).
+bool gs_stream_passes_supported_f32(const BlasPlan& plan, int64_t n, int nvec_max);
+bool gs_stream_passes_supported_bf16(const BlasPlan& plan, int64_t n, int nvec_max);
 
 // Fused block Gram-Schmidt pass over nvec basis vectors v_i = basis + i * vstride:
 //   if update: w <- w - sum_i coef[i][r] v_i   (coef: device double2 [nvec][nrhs])
@@ -68,15 +65,11 @@ bool gs_stream_fin_supported_bf16(const BlasPlan& plan, int64_t n, int nvec_max)
 //   (dots and norm refer to the unscaled w). With neither dots nor norm no reduction runs.
 //   basis_bf16: basis stored as BF16 pairs (FP32 arithmetic, w in FP32; needs nrhs <= 32);
 //   wout: optional, the scaled updated w is stored there (in the basis storage type) instead of in w.
-//   coef2 (optional, device double2 [nvec - 1][nrhs], with oscale2 [nrhs]; a dots + norm pass
-//   without update, the streaming kernel, FP32 or BF16): in the same pass the last basis
-//   vector is replaced in place by (v_{nvec-1} - sum_{i < nvec-1} coef2_i v_i) * oscale2 (the
-//   dots use the old v_{nvec-1}); cudaErrorNotSupported if the streaming kernel cannot run it.
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,
                            bool norm, void* partials, void* out, const int* skip,
                            cudaStream_t stream, const double* oscale = nullptr, bool basis_bf16 = false,
-                           void* wout = nullptr, const void* coef2 = nullptr, const double* oscale2 = nullptr);
+                           void* wout = nullptr);
 
 // r = b - t (b, r FP64; t FP64, or FP32 when t_f32) with out[0][r] = ||r||^2.
 cudaError_t launch_sub_norm(const BlasPlan& plan, int64_t n, const void* b, const void* t, void* r,

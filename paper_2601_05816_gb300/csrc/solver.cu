@@ -137,144 +137,219 @@ __global__ void givens_kernel(GmresState s, int j, const double2* __restrict__ h
 // ---------------------------------------------------------------- delayed CGS2
 //
 // Classical Gram-Schmidt with the re-orthogonalisation delayed by one step, so that
-// each Arnoldi step reads the basis twice instead of three times. At step j the basis
-// holds the final q_0 .. q_{j-1} (Q_j) and a once-orthogonalised candidate
-// q~_j = Q_j a_j + rho_j q_j (a_j, rho_j known from the previous step), and w = A q~_j:
-//   pass A: e = [Q_j, q~_j]^H w, omega = ||w||^2, and in the same pass q_j =
-//           (q~_j - Q_j a_j) / rho_j in place (the dots use the old slot);
-//   coef2:  b = e_{<j}, c = q_j^H w = (e_j - a_j^H b) / rho_j, nu^2 = omega - |b|^2 - |c|^2
-//           (Pythagoras; nu only normalises the next candidate, its error is absorbed
-//           one step later);
-//   pass B: q~_{j+1} = (w - Q_j b - q_j c) / nu, d = Q_{j+1}^H (nu q~_{j+1}), ||nu q~_{j+1}||^2;
-//   coef1:  a_{j+1} = d / nu, rho_{j+1}^2 = ||q~_{j+1}||^2 - |a_{j+1}|^2, and Hessenberg
-//           column j: A q_j = (A q~_j - A Q_j a_j) / rho_j with q~_{j+1} = Q_{j+1} a_{j+1} +
-//           rho_{j+1} q_{j+1} gives
-//           H_{l,j} = (bc_l + nu a_{j+1,l} - (H_{:,<j} a_j)_l) / rho_j (l <= j), H_{j+1,j} = nu rho_{j+1} / rho_j
-//           (bc = [b; c], H_{:,<j} the unrotated earlier columns), then its Givens step and the
-//           stop test - before the next operator apply, so finished rhs skip it.
-// One warp per rhs (a CTA of 32 nrhs threads, up to 32 rhs per warp row), lanes over the
-// basis index; sums over lanes in a fixed shuffle order.
+// each Arnoldi step reads the basis twice instead of three times. The basis slots keep
+// the once-orthogonalised candidates q~_0 .. q~_j (q~_0 = q_0 = r / ||r||); with the
+// orthonormal basis Q they satisfy Q~_{j+1} = Q_{j+1} T_{j+1}, T upper triangular with
+// columns [a_i; rho_i] (q~_i = Q_i a_i + rho_i q_i). Q is never formed. At step j, w = A q~_j:
+//   pass A: e = Q~_{j+1}^H w, omega = ||w||^2;
+//   coef2:  z = Q_{j+1}^H w = T^{-H} e (= [b; c], the projection on the final basis),
+//           nu^2 = omega - |z|^2 (Pythagoras; nu only normalises the next candidate, its
+//           error is absorbed one step later), g = T^{-1} z;
+//   pass B: q~_{j+1} = (w - Q~_{j+1} g) / nu = (w - Q_{j+1} z) / nu, d = Q~_{j+1}^H (nu q~_{j+1}),
+//           ||nu q~_{j+1}||^2;
+//   coef1:  a_{j+1} = T^{-H} d / nu, rho_{j+1}^2 = ||q~_{j+1}||^2 - |a_{j+1}|^2 (T grows by a
+//           column), and Hessenberg column j: A q_j = (A q~_j - A Q_j a_j) / rho_j with
+//           q~_{j+1} = Q_{j+1} a_{j+1} + rho_{j+1} q_{j+1} gives
+//           H_{l,j} = (z_l + nu a_{j+1,l} - (H_{:,<j} a_j)_l) / rho_j (l <= j), H_{j+1,j} = nu rho_{j+1} / rho_j
+//           (H_{:,<j} the unrotated earlier columns), then its Givens step and the stop test,
+//           before the next operator apply (finished rhs skip it).
+// After the cycle x += Q_k y = Q~_k (T_k^{-1} y). One warp per rhs, lane l on basis index l
+// (restart length <= 32); the triangular solves run over the lanes with shuffles.
 struct DcgsState {
   double2* Hraw;    // [nrhs][m][m + 1] unrotated final columns
-  double2* bc;      // [nrhs][m + 1] pending [b; c]
-  double2* a_cur;   // [nrhs][m] a_j of the current candidate
-  double2* a_pend;  // [nrhs][m] a_j of the pending column
-  double* rho_cur;  // [nrhs]
-  double* rho_pend; // [nrhs]
-  double* nu_pend;  // [nrhs]
+  double2* T;       // [nrhs][m + 1][m + 1] column-major: T[c][l], l <= c
+  double2* z;       // [nrhs][m + 1] pending projection z of the current step
+  double* nu;       // [nrhs]
   double2* g;       // [m + 1][nrhs] pass-B update coefficients
-  double2* acoef;   // [m][nrhs] pass-A finalisation coefficients (a_j)
-  double* scale2;   // [nrhs] 1 / rho_j
+  unsigned* ctr;    // [2] live-rhs count and CTA ticket of the column kernel (0 between launches)
 };
+
+// One CTA (one warp) per rhs; the triangular factor and the Hessenberg columns are staged
+// in shared memory, so that the sequential substitutions wait on shuffles, not on loads.
+constexpr int kDcgsMaxM = 32;
+constexpr int kDcgsLd = kDcgsMaxM + 1;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
-
-// coef1 after pass B of step jn - 1 (dd: Q_jn^H (nu q~_jn) in slots 0 .. jn-1, the norm in slot
-// jn): a_jn, rho_jn, final column jn - 1 and its Givens step. Lane l handles basis index l
-// (the restart length is at most 32).
-__global__ void dcgs_coef1_kernel(GmresState s, DcgsState d, int jn, const double2* __restrict__ dd) {
-  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
-  const int nrhs = s.nrhs, m = s.m;
-  bool live = false;
-  if (r < nrhs && s.done[r]) {  // finished rhs: its next slot stays as it is (finite, unused)
-    if (lane < jn) d.acoef[(int64_t)lane * nrhs + r] = make_double2(0.0, 0.0);
-    if (lane == 0) d.scale2[r] = 1.0;
-  } else if (r < nrhs) {
-    const double nu = d.nu_pend[r], rho_p = d.rho_pend[r];
-    const double inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
-    double2* a = d.a_cur + (int64_t)r * m;
-    const double2* ap = d.a_pend + (int64_t)r * m;
-    double2 al = make_double2(0.0, 0.0);
-    if (lane < jn) {
-      al = dd[(int64_t)lane * nrhs + r];
-      al.x *= inv_nu;
-      al.y *= inv_nu;
-      a[lane] = al;
-    }
-    const double asq = warp_sum(al.x * al.x + al.y * al.y);
-    const double alpha = dd[(int64_t)jn * nrhs + r].x * inv_nu * inv_nu;
-    const double rho = sqrt(fmax(alpha - asq, 0.0));
-    // column j = jn - 1, row l = lane
-    const int j = jn - 1;
-    const double2* bc = d.bc + (int64_t)r * (m + 1);
-    double2* raw = d.Hraw + ((int64_t)r * m + j) * (m + 1);
-    double2 v = make_double2(0.0, 0.0);
-    if (lane <= j) {
-      v = make_double2(bc[lane].x + nu * al.x, bc[lane].y + nu * al.y);
-      for (int k = (lane > 0 ? lane - 1 : 0); k < j; ++k) {  // column k has rows 0 .. k + 1
-        const double2 h = d.Hraw[((int64_t)r * m + k) * (m + 1) + lane], ak = ap[k];
-        v.x -= h.x * ak.x - h.y * ak.y;
-        v.y -= h.x * ak.y + h.y * ak.x;
-      }
-      v.x /= rho_p;
-      v.y /= rho_p;
-      raw[lane] = v;
-    }
-    const double beta = nu * rho / rho_p;
-    const double w2 = warp_sum(v.x * v.x + v.y * v.y) + beta * beta;
-    __syncwarp();
-    int go = 0;
-    if (lane == 0) {
-      raw[j + 1] = make_double2(beta, 0.0);
-      double2* col = s.H + ((int64_t)r * m + j) * (m + 1);
-      for (int l = 0; l <= j; ++l) col[l] = raw[l];
-      go = givens_step(s, r, j, col, beta, w2) && rho > 0.0 && isfinite(rho);
-      if (!go) s.done[r] = 1;
-      d.rho_cur[r] = rho;
-      d.scale2[r] = go ? 1.0 / rho : 1.0;
-    }
-    go = __shfl_sync(0xffffffffu, go, 0);
-    if (lane < jn) d.acoef[(int64_t)lane * nrhs + r] = go ? al : make_double2(0.0, 0.0);
-    live = go != 0;
-  }
-  const int any = __syncthreads_or(live && lane == 0);
-  if (threadIdx.x == 0) *s.all_done = any ? 0 : 1;
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// coef2 after pass A of step j (e: [Q_j, q~_j]^H w in slots 0 .. j, ||w||^2 in slot j + 1):
-// c, nu, the pass-B coefficients g = [b; c] and the pending column.
-__global__ void dcgs_coef2_kernel(GmresState s, DcgsState d, int j, const double2* __restrict__ e) {
-  const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
-  const int nrhs = s.nrhs, m = s.m;
-  if (r >= nrhs) return;
+// Columns 0 .. n-1 of T (upper triangle) into Ts[c][l], reciprocals of the (real) diagonal.
+__device__ __forceinline__ void stage_T(const double2* __restrict__ T, int ldt, int n, int lane,
+                                        double2 (*Ts)[kDcgsLd], double* inv_d) {
+#pragma unroll 4
+  for (int c = 0; c < n; ++c)
+    if (lane <= c) Ts[c][lane] = T[(int64_t)c * ldt + lane];
+  __syncwarp();
+  if (lane < n) inv_d[lane] = 1.0 / Ts[lane][lane].x;
+  __syncwarp();
+}
+
+// x = T^{-H} v for the n x n leading block (lane l holds v_l on entry, x_l on return):
+// forward substitution with the lower-triangular T^H, (T^H)_{l,i} = conj(T_{i,l}).
+__device__ double2 solve_TH(const double2 (*Ts)[kDcgsLd], const double* inv_d, int n, int lane, double2 v) {
+  for (int i = 0; i < n; ++i) {
+    double2 xi = shfl2(v, i);
+    const double di = inv_d[i];
+    xi.x *= di;
+    xi.y *= di;
+    if (lane == i) {
+      v = xi;
+    } else if (lane > i && lane < n) {
+      const double2 t = Ts[lane][i];  // T_{i,lane}
+      v.x -= t.x * xi.x + t.y * xi.y;
+      v.y -= t.x * xi.y - t.y * xi.x;
+    }
+  }
+  return v;
+}
+// x = T^{-1} v (back substitution with the upper-triangular T).
+__device__ double2 solve_T(const double2 (*Ts)[kDcgsLd], const double* inv_d, int n, int lane, double2 v) {
+  for (int i = n - 1; i >= 0; --i) {
+    double2 xi = shfl2(v, i);
+    const double di = inv_d[i];
+    xi.x *= di;
+    xi.y *= di;
+    if (lane == i) {
+      v = xi;
+    } else if (lane < i) {
+      const double2 t = Ts[i][lane];  // T_{lane,i}
+      v.x -= t.x * xi.x - t.y * xi.y;
+      v.y -= t.x * xi.y + t.y * xi.x;
+    }
+  }
+  return v;
+}
+
+// coef2 after pass A of step j (e: Q~_{j+1}^H w in slots 0 .. j, ||w||^2 in slot j + 1).
+__global__ void __launch_bounds__(32) dcgs_coef2_kernel(GmresState s, DcgsState d, int j,
+                                                        const double2* __restrict__ e) {
+  __shared__ double2 Ts[kDcgsMaxM][kDcgsLd];
+  __shared__ double inv_d[kDcgsMaxM];
+  const int lane = threadIdx.x, r = blockIdx.x;
+  const int nrhs = s.nrhs, m = s.m, n = j + 1;
+  double2* T = d.T + (int64_t)r * (m + 1) * (m + 1);
   if (s.done[r]) {  // finished rhs: next candidate 0
     if (lane <= j) d.g[(int64_t)lane * nrhs + r] = make_double2(0.0, 0.0);
     if (lane == 0) s.scale[r] = 0.0;
     return;
   }
-  const double rho = j == 0 ? 1.0 : d.rho_cur[r];
-  const double2* a = d.a_cur + (int64_t)r * m;
-  double2 bl = make_double2(0.0, 0.0), aa = make_double2(0.0, 0.0);
-  if (lane < j) {
-    bl = e[(int64_t)lane * nrhs + r];
-    aa = a[lane];
+  if (j == 0) {
+    if (lane == 0) {
+      T[0] = make_double2(1.0, 0.0);
+      Ts[0][0] = make_double2(1.0, 0.0);
+      inv_d[0] = 1.0;
+    }
+    __syncwarp();
+  } else {
+    stage_T(T, m + 1, n, lane, Ts, inv_d);
   }
-  const double abx = warp_sum(aa.x * bl.x + aa.y * bl.y), aby = warp_sum(aa.x * bl.y - aa.y * bl.x);
-  const double bsq = warp_sum(bl.x * bl.x + bl.y * bl.y);
-  const double2 ej = e[(int64_t)j * nrhs + r];
-  const double2 c = make_double2((ej.x - abx) / rho, (ej.y - aby) / rho);
+  const double2 v = lane <= j ? e[(int64_t)lane * nrhs + r] : make_double2(0.0, 0.0);
+  const double2 z = solve_TH(Ts, inv_d, n, lane, v);
+  const double zsq = warp_sum(lane <= j ? z.x * z.x + z.y * z.y : 0.0);
   const double omega = e[(int64_t)(j + 1) * nrhs + r].x;
-  const double nu = sqrt(fmax(omega - bsq - (c.x * c.x + c.y * c.y), 1e-12 * omega));
-  double2* bc = d.bc + (int64_t)r * (m + 1);
-  double2* ap = d.a_pend + (int64_t)r * m;
-  if (lane < j) {
-    bc[lane] = bl;
-    ap[lane] = aa;
-    d.g[(int64_t)lane * nrhs + r] = bl;
+  const double nu = sqrt(fmax(omega - zsq, 1e-12 * omega));
+  const double2 g = solve_T(Ts, inv_d, n, lane, z);
+  if (lane <= j) {
+    d.z[(int64_t)r * (m + 1) + lane] = z;
+    d.g[(int64_t)lane * nrhs + r] = g;
   }
   if (lane == 0) {
-    bc[j] = c;
-    d.g[(int64_t)j * nrhs + r] = c;
-    d.nu_pend[r] = nu;
-    d.rho_pend[r] = rho;
+    d.nu[r] = nu;
     const bool ok = isfinite(nu) && nu > 0.0;
     s.scale[r] = ok ? 1.0 / nu : 0.0;
     if (!ok) s.done[r] = 1;
   }
+}
+
+// coef1 after pass B of step j (dd: Q~_{j+1}^H (nu q~_{j+1}) in slots 0 .. j, the norm in
+// slot j + 1): the new column of T, final Hessenberg column j and its Givens step. The last
+// CTA to finish sets the all-finished flag from the count of live rhs.
+__global__ void __launch_bounds__(32) dcgs_coef1_kernel(GmresState s, DcgsState d, int j,
+                                                        const double2* __restrict__ dd) {
+  __shared__ double2 Ts[kDcgsMaxM][kDcgsLd];
+  __shared__ double2 Hs[kDcgsMaxM][kDcgsLd];
+  __shared__ double inv_d[kDcgsMaxM];
+  const int lane = threadIdx.x, r = blockIdx.x;
+  const int nrhs = s.nrhs, m = s.m, n = j + 1;
+  int go = 0;
+  if (!s.done[r]) {
+    double2* T = d.T + (int64_t)r * (m + 1) * (m + 1);
+    const double2* Hr = d.Hraw + (int64_t)r * m * (m + 1);
+    stage_T(T, m + 1, n, lane, Ts, inv_d);
+#pragma unroll 4
+    for (int k = 0; k < j; ++k)  // column k has rows 0 .. k + 1
+      if (lane <= k + 1) Hs[k][lane] = Hr[(int64_t)k * (m + 1) + lane];
+    __syncwarp();
+    const double nu = d.nu[r];
+    const double inv_nu = nu > 0.0 ? 1.0 / nu : 0.0;
+    double2 v = lane <= j ? dd[(int64_t)lane * nrhs + r] : make_double2(0.0, 0.0);
+    v.x *= inv_nu;
+    v.y *= inv_nu;
+    const double2 an = solve_TH(Ts, inv_d, n, lane, v);  // a_{j+1}
+    const double asq = warp_sum(lane <= j ? an.x * an.x + an.y * an.y : 0.0);
+    const double alpha = dd[(int64_t)(j + 1) * nrhs + r].x * inv_nu * inv_nu;
+    const double rho_n = sqrt(fmax(alpha - asq, 0.0));
+    const double inv_rho_j = inv_d[j];  // 1 / rho_j
+    double2 h = make_double2(0.0, 0.0);
+    if (lane <= j) {
+      const double2 zl = d.z[(int64_t)r * (m + 1) + lane];
+      h = make_double2(zl.x + nu * an.x, zl.y + nu * an.y);
+      for (int k = (lane > 0 ? lane - 1 : 0); k < j; ++k) {
+        const double2 hk = Hs[k][lane];
+        const double2 ak = Ts[j][k];  // a_j = T[0 .. j-1, j]
+        h.x -= hk.x * ak.x - hk.y * ak.y;
+        h.y -= hk.x * ak.y + hk.y * ak.x;
+      }
+      h.x *= inv_rho_j;
+      h.y *= inv_rho_j;
+      d.Hraw[((int64_t)r * m + j) * (m + 1) + lane] = h;
+      Hs[j][lane] = h;
+    }
+    const double beta = nu * rho_n * inv_rho_j;
+    const double w2 = warp_sum(h.x * h.x + h.y * h.y) + beta * beta;
+    // the new column of T (used from the next step on)
+    if (lane <= j) T[(int64_t)(j + 1) * (m + 1) + lane] = an;
+    __syncwarp();
+    if (lane == 0) {
+      T[(int64_t)(j + 1) * (m + 1) + j + 1] = make_double2(rho_n, 0.0);
+      d.Hraw[((int64_t)r * m + j) * (m + 1) + j + 1] = make_double2(beta, 0.0);
+      double2* col = s.H + ((int64_t)r * m + j) * (m + 1);
+      for (int l = 0; l <= j; ++l) col[l] = Hs[j][l];
+      go = givens_step(s, r, j, col, beta, w2) && rho_n > 0.0 && isfinite(rho_n);
+      if (!go) s.done[r] = 1;
+    }
+  }
+  if (lane == 0) {
+    if (go) atomicAdd(&d.ctr[0], 1u);
+    __threadfence();
+    const unsigned ticket = atomicAdd(&d.ctr[1], 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      const unsigned live = atomicAdd(&d.ctr[0], 0u);
+      *s.all_done = live ? 0 : 1;
+      d.ctr[0] = 0u;
+      d.ctr[1] = 0u;
+    }
+  }
+}
+
+// After the back substitution: y <- T_k^{-1} y per rhs (x += Q~_k T_k^{-1} y).
+__global__ void __launch_bounds__(32) dcgs_y_kernel(GmresState s, DcgsState d) {
+  __shared__ double2 Ts[kDcgsMaxM][kDcgsLd];
+  __shared__ double inv_d[kDcgsMaxM];
+  const int lane = threadIdx.x, r = blockIdx.x;
+  const int nrhs = s.nrhs, m = s.m;
+  const int k = s.k[r];
+  if (k == 0) return;
+  stage_T(d.T + (int64_t)r * (m + 1) * (m + 1), m + 1, k, lane, Ts, inv_d);
+  double2 v = lane < k ? s.y[(int64_t)lane * nrhs + r] : make_double2(0.0, 0.0);
+  v = solve_T(Ts, inv_d, k, lane, v);
+  if (lane < k) s.y[(int64_t)lane * nrhs + r] = v;
 }
 
 // Back substitution R y = gamma per rhs; y stored [m][nrhs]; kmax = max_r k_r.
@@ -329,14 +404,18 @@ cudaError_t launch_givens(const GmresState& s, int j, const void* h1, const void
                                                          (const double2*)hn, pythag ? 1 : 0);
   return cudaGetLastError();
 }
-static cudaError_t launch_dcgs_coef1(const GmresState& s, const DcgsState& d, int jn, const void* dd,
+static cudaError_t launch_dcgs_coef1(const GmresState& s, const DcgsState& d, int j, const void* dd,
                                      cudaStream_t stream) {
-  dcgs_coef1_kernel<<<1, 32 * s.nrhs, 0, stream>>>(s, d, jn, (const double2*)dd);
+  dcgs_coef1_kernel<<<s.nrhs, 32, 0, stream>>>(s, d, j, (const double2*)dd);
   return cudaGetLastError();
 }
 static cudaError_t launch_dcgs_coef2(const GmresState& s, const DcgsState& d, int j, const void* e,
                                      cudaStream_t stream) {
-  dcgs_coef2_kernel<<<1, 32 * s.nrhs, 0, stream>>>(s, d, j, (const double2*)e);
+  dcgs_coef2_kernel<<<s.nrhs, 32, 0, stream>>>(s, d, j, (const double2*)e);
+  return cudaGetLastError();
+}
+static cudaError_t launch_dcgs_y(const GmresState& s, const DcgsState& d, cudaStream_t stream) {
+  dcgs_y_kernel<<<s.nrhs, 32, 0, stream>>>(s, d);
   return cudaGetLastError();
 }
 cudaError_t launch_backsub(const GmresState& s, cudaStream_t stream) {
@@ -381,17 +460,16 @@ static lqcd_status arnoldi_ortho(const SolveBufs& b, int j, bool reorth, cudaEve
   const int64_t vstride = b.n_sys;
   const int* skip = b.st.all_done;
   if (b.ortho == 2) {
-    // delayed CGS2: pass A (dots + norm of w, q_j finalised in place), coefficients, pass B
-    // (the next candidate, its dots and norm), then the final column j and its Givens step
+    // delayed CGS2: pass A (dots + norm of w), coefficients, pass B (the next candidate, its
+    // dots and norm), then the final column j and its Givens step
     LQCD_CUDA(launch_gs_pass(false, b.plan, b.n_sys, nvec, b.basis, vstride, w, nullptr, false, true, true,
-                             b.partials, b.h1, skip, s, nullptr, b.bf16, nullptr,
-                             j > 0 ? (const void*)b.dc.acoef : nullptr, b.dc.scale2),
+                             b.partials, b.h1, skip, s, nullptr, b.bf16),
               "dcgs pass A");
     LQCD_CUDA(launch_dcgs_coef2(b.st, b.dc, j, b.h1, s), "dcgs coefficients");
     LQCD_CUDA(launch_gs_pass(false, b.plan, b.n_sys, nvec, b.basis, vstride, w, b.dc.g, true, true, true,
                              b.partials, b.h2, skip, s, b.st.scale, b.bf16, b.bf16 ? next : nullptr),
               "dcgs pass B");
-    LQCD_CUDA(launch_dcgs_coef1(b.st, b.dc, j + 1, b.h2, s), "dcgs column");
+    LQCD_CUDA(launch_dcgs_coef1(b.st, b.dc, j, b.h2, s), "dcgs column");
     if (ev_gs_end) LQCD_CUDA(cudaEventRecord(ev_gs_end, s), "event");
     return LQCD_OK;
   }
@@ -450,8 +528,8 @@ static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int 
 static double gs_algorithmic_bytes(int64_t n, int nvec, bool f64, int ortho, bool bf16 = false) {
   const double vb = (double)n * (bf16 ? 4.0 : (f64 ? 16.0 : 8.0));  // a basis vector
   const double vw = (double)n * (f64 ? 16.0 : 8.0);                  // w (FP32 for a BF16 basis)
-  if (ortho == 2)  // delayed CGS2: two reads of the basis and w; writes the candidate and, from step 1, q_j
-    return 2 * (nvec * vb + vw) + vb + (nvec > 1 ? vb : 0.0);
+  if (ortho == 2)  // delayed CGS2: two reads of the basis and w, one write of the next candidate
+    return 2 * (nvec * vb + vw) + vb;
   if (bf16)  // CGS2 with a BF16 basis; the last pass writes the BF16 basis vector
     return (nvec * vb + vw) + (nvec * vb + 2 * vw) + (nvec * vb + vw + vb);
   const double dots = (nvec + 1) * vw, upd = (nvec + 2) * vw;
@@ -609,8 +687,9 @@ struct SolveJob {
   lqcd_status enqueue_cycle(cudaStream_t cs, bool allow_graph);
   lqcd_status finish();
   // kernels of one restart cycle: cycle_init, v0, per step (operator, Gram-Schmidt
-  // passes with their reductions, givens, normalisation), backsub, update
-  long long cycle_launches() const { return 4 + (long long)m * ((eo ? 2 : 1) + 6); }
+  // passes with their reductions, givens, normalisation), backsub (and the delayed-CGS2
+  // change of basis of y), update
+  long long cycle_launches() const { return 4 + (B.ortho == 2 ? 1 : 0) + (long long)m * ((eo ? 2 : 1) + 6); }
 };
 
 lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr, const void* bb, void* xx,
@@ -684,18 +763,18 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   B.plan = blas_plan(n_sys, nrhs, ctx->num_sms);
   B.plan.wait_flag = wait_flag(ctx);
   // delayed CGS2 needs the streaming Gram-Schmidt kernel for every basis size (FP32 or
-  // BF16 basis, restart length <= 32) and one warp per rhs (nrhs <= 32); otherwise CGS2
+  // BF16 basis) and restart length <= 32 (one warp per rhs in the coefficient kernels); otherwise CGS2
   B.ortho = ortho_req;
-  if (B.ortho == 2 && (f64_inner || m > 32 || nrhs > 32 ||
-                       !(bf16 ? gs_stream_fin_supported_bf16(B.plan, n_sys, m) : gs_stream_fin_supported_f32(B.plan, n_sys, m))))
+  if (B.ortho == 2 && (f64_inner || m > kDcgsMaxM ||
+                       !(bf16 ? gs_stream_passes_supported_bf16(B.plan, n_sys, m)
+                              : gs_stream_passes_supported_f32(B.plan, n_sys, m))))
     B.ortho = 1;
   memset(&B.dc, 0, sizeof(B.dc));
   if (B.ortho == 2) {
-    const size_t dpiece[10] = {sizeof(double2) * (size_t)nrhs * m * (m + 1), sizeof(double2) * (size_t)nrhs * (m + 1),
-                               sizeof(double2) * (size_t)nrhs * m, sizeof(double2) * (size_t)nrhs * m,
-                               sizeof(double) * nrhs, sizeof(double) * nrhs, sizeof(double) * nrhs,
-                               sizeof(double2) * (size_t)(m + 1) * nrhs, sizeof(double2) * (size_t)m * nrhs,
-                               sizeof(double) * nrhs};
+    const size_t dpiece[6] = {sizeof(double2) * (size_t)nrhs * m * (m + 1),
+                              sizeof(double2) * (size_t)nrhs * (m + 1) * (m + 1),
+                              sizeof(double2) * (size_t)nrhs * (m + 1), sizeof(double) * nrhs,
+                              sizeof(double2) * (size_t)(m + 1) * nrhs, 2 * sizeof(unsigned)};
     size_t dbytes = 0;
     for (size_t q : dpiece) dbytes += (q + 255) & ~(size_t)255;
     void* dmem;
@@ -704,15 +783,12 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     int next = 0;
     auto take = [&]() { void* q = p; p += (dpiece[next++] + 255) & ~(size_t)255; return q; };
     B.dc.Hraw = (double2*)take();
-    B.dc.bc = (double2*)take();
-    B.dc.a_cur = (double2*)take();
-    B.dc.a_pend = (double2*)take();
-    B.dc.rho_cur = (double*)take();
-    B.dc.rho_pend = (double*)take();
-    B.dc.nu_pend = (double*)take();
+    B.dc.T = (double2*)take();
+    B.dc.z = (double2*)take();
+    B.dc.nu = (double*)take();
     B.dc.g = (double2*)take();
-    B.dc.acoef = (double2*)take();
-    B.dc.scale2 = (double*)take();
+    B.dc.ctr = (unsigned*)take();
+    LQCD_CUDA(cudaMemsetAsync(B.dc.ctr, 0, 2 * sizeof(unsigned), stream), "dcgs counters");
   }
   const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
   if ((st = workspace(ctx, "solve_partials", hb * B.plan.blocks, &B.partials)) != LQCD_OK) return st;
@@ -920,6 +996,7 @@ lqcd_status SolveJob::enqueue_cycle(cudaStream_t cs, bool allow_graph) {
     if ((st = run_cycle_direct(ctx, B, P.op, reorth, &prof, cs)) != LQCD_OK) return st;
   }
   LQCD_CUDA(launch_backsub(B.st, cs), "backsub");
+  if (B.ortho == 2) LQCD_CUDA(launch_dcgs_y(B.st, B.dc, cs), "dcgs y");
   LQCD_CUDA(launch_update_x(f64_inner, n_sys, nrhs, m, B.basis, n_sys, B.st.y, B.st.kmax, sys_x, cs, bf16),
             "update x");
   nl += cycle_launches();
@@ -962,6 +1039,7 @@ lqcd_status SolveJob::finish() {
     stats->ortho_bytes = prof.gs_bytes;
     stats->kernel_launches = nl;
     stats->outer_steps = outer_steps;
+    stats->ortho = B.ortho;
     if (stats->iters_per_rhs) for (int r = 0; r < nrhs; ++r) stats->iters_per_rhs[r] = iters[r];
     if (stats->relres_per_rhs) for (int r = 0; r < nrhs; ++r) stats->relres_per_rhs[r] = relres[r];
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
