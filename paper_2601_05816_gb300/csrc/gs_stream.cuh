@@ -234,6 +234,14 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
     }
   } else {
     // ---------------- consumers
+    // with one rhs per lane the lane's update coefficients are the same for every element
+    // it visits: kept in registers (one shared-memory read per basis element fewer) where
+    // the instance has the registers to spare (the 16- and 32-vector ones would spill)
+    constexpr bool kCoefRegs = UPDATE && EPL == 1 && (NV == 8 || NV == 24);
+    C cr[kCoefRegs ? NV : 1];
+#pragma unroll
+    for (int i = 0; i < (kCoefRegs ? NV : 1); ++i)
+      cr[i] = (kCoefRegs && i < nvec && lane_on) ? cs[i * nrhs + r] : make_float2(0.f, 0.f);
     for (int l = 0; l < L; ++l) {
       const int s = l % S;
       if (!mbar_wait_bounded(&full[s], (uint32_t)(l / S) & 1u)) {
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               lds<EPL>(vt + (size_t)i * vte + e, v);
 #pragma unroll
               for (int q = 0; q < EPL; ++q) {
-                const C c = cs[i * nrhs + r + q];
+                const C c = kCoefRegs ? cr[i] : cs[i * nrhs + r + q];
                 pr[i & 3][q] += c.x * v[q].x - c.y * v[q].y;
                 pi[i & 3][q] += c.x * v[q].y + c.y * v[q].x;
               }

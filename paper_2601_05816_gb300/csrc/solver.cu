@@ -54,13 +54,17 @@ __global__ void cycle_init_kernel(GmresState s, const double* __restrict__ beta0
 // sub-diagonal entry beta, gamma_{j+1} = -conj(s) gamma_j, gamma_j = c gamma_j,
 // and the stop test (|gamma_{j+1}| <= thr, happy breakdown beta <= 1e-14 ||column||,
 // the last column, or a non-finite value). Returns whether the cycle goes on.
-__device__ bool givens_step(const GmresState& s, int r, int j, double2* col, double beta, double w2) {
+// cs_prev / sn_prev: optional copies of the earlier rotations (e.g. staged in shared memory).
+__device__ bool givens_step(const GmresState& s, int r, int j, double2* col, double beta, double w2,
+                            const double* cs_prev = nullptr, const double2* sn_prev = nullptr) {
   double* cs = s.cs + (int64_t)r * s.m;
   double2* sn = s.sn + (int64_t)r * s.m;
+  const double* csr = cs_prev ? cs_prev : cs;
+  const double2* snr = sn_prev ? sn_prev : sn;
   for (int i = 0; i < j; ++i) {
     const double2 top = col[i], bot = col[i + 1];
-    const double c = cs[i];
-    const double2 sv = sn[i];
+    const double c = csr[i];
+    const double2 sv = snr[i];
     // top' = c top + s bot ; bot' = -conj(s) top + c bot
     col[i] = make_double2(c * top.x + sv.x * bot.x - sv.y * bot.y, c * top.y + sv.x * bot.y + sv.y * bot.x);
     col[i + 1] = make_double2(-(sv.x * top.x + sv.y * top.y) + c * bot.x,
@@ -274,12 +278,18 @@ __global__ void __launch_bounds__(32) dcgs_coef1_kernel(GmresState s, DcgsState 
   __shared__ double2 Ts[kDcgsMaxM][kDcgsLd];
   __shared__ double2 Hs[kDcgsMaxM][kDcgsLd];
   __shared__ double inv_d[kDcgsMaxM];
+  __shared__ double cs_s[kDcgsMaxM];
+  __shared__ double2 sn_s[kDcgsMaxM];
   const int lane = threadIdx.x, r = blockIdx.x;
   const int nrhs = s.nrhs, m = s.m, n = j + 1;
   int go = 0;
   if (!s.done[r]) {
     double2* T = d.T + (int64_t)r * (m + 1) * (m + 1);
     const double2* Hr = d.Hraw + (int64_t)r * m * (m + 1);
+    if (lane < j) {  // the earlier rotations, for the Givens step below
+      cs_s[lane] = s.cs[(int64_t)r * m + lane];
+      sn_s[lane] = s.sn[(int64_t)r * m + lane];
+    }
     stage_T(T, m + 1, n, lane, Ts, inv_d);
 #pragma unroll 4
     for (int k = 0; k < j; ++k)  // column k has rows 0 .. k + 1
@@ -318,11 +328,12 @@ __global__ void __launch_bounds__(32) dcgs_coef1_kernel(GmresState s, DcgsState 
     if (lane == 0) {
       T[(int64_t)(j + 1) * (m + 1) + j + 1] = make_double2(rho_n, 0.0);
       d.Hraw[((int64_t)r * m + j) * (m + 1) + j + 1] = make_double2(beta, 0.0);
-      double2* col = s.H + ((int64_t)r * m + j) * (m + 1);
-      for (int l = 0; l <= j; ++l) col[l] = Hs[j][l];
-      go = givens_step(s, r, j, col, beta, w2) && rho_n > 0.0 && isfinite(rho_n);
+      // rotate the shared-memory copy of the column, then store it
+      go = givens_step(s, r, j, Hs[j], beta, w2, cs_s, sn_s) && rho_n > 0.0 && isfinite(rho_n);
       if (!go) s.done[r] = 1;
     }
+    __syncwarp();
+    if (lane <= j) s.H[((int64_t)r * m + j) * (m + 1) + lane] = Hs[j][lane];
   }
   if (lane == 0) {
     if (go) atomicAdd(&d.ctr[0], 1u);
