@@ -63,11 +63,14 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) per Gram-Schmidt step of the timed solve, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the streaming Gram-Schmidt launches of
-# a full 32-step Arnoldi cycle of the default workload, keyed by (workload, precision,
-# Gram-Schmidt variant); the summaries are under profiles/. Cases not captured report null.
-GS_TRAFFIC_PER_STEP = {("solve", "c64", 1): 5.36e9}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and algorithmic bytes of the
+# streaming Gram-Schmidt launches of one full 32-step Arnoldi cycle (64 launches, 1 .. 32
+# basis vectors) of the default workload, from one ncu capture each, keyed by (workload,
+# precision, Gram-Schmidt variant); the summaries are under profiles/. The reported traffic
+# per step is the timed solve's algorithmic bytes per step times their ratio (the timed
+# steps have a different mix of basis sizes than one full cycle). Cases not captured: null.
+GS_DRAM_CAPTURE = {("solve", "c64", 2): (115.67273088e9, 1152 * 100663296.0),
+                   ("solve", "bf16", 2): (60.980819968e9, 1216 * 50331648.0)}
 
 
 def measured_peaks():
@@ -530,7 +533,7 @@ def run_gpu(args, w):
     peak, peak_kind = measured_peaks()
     inner = {"c64": lq.C64, "bf16": lq.BF16S}[args.precision]
     solve_kw = dict(op=lq.OP_SCHUR, precision=inner, restart_len=w["restart"], tol=w["tol"],
-                    max_restarts=args.max_restarts, use_graph=True, profile=True)
+                    max_restarts=args.max_restarts, use_graph=True, profile=True, reorth=args.reorth)
 
     # set-up: autotune the hopping kernel for the inner (FP32) and outer (FP64) operators
     lat.set_gauge(U_d)
@@ -578,8 +581,13 @@ def run_gpu(args, w):
                            1: "gs_pass (CGS2 step: 3 fused passes)"}.get(ortho, "gs_pass (CGS1 step)"),
                    ms=gs_ms, n=sum(r.ortho_launches for r in results),
                    bytes=sum(r.ortho_bytes for r in results),
-                   traffic=GS_TRAFFIC_PER_STEP.get((args.workload, args.precision, ortho))
+                   capture=GS_DRAM_CAPTURE.get((args.workload, args.precision, ortho))
                    if "m0_prescribed" not in w else None)
+        if dom["capture"] is not None and dom["n"] > 0:
+            dram, alg = dom["capture"]
+            dom["traffic"] = dom["bytes"] / dom["n"] * dram / alg
+        else:
+            dom["traffic"] = None
     else:
         dom = dict(kernel="dslash (Schur apply: passes A + B)", ms=op_ms, n=sum(r.op_launches for r in results),
                    bytes=sum(r.op_bytes for r in results), traffic=None)
@@ -603,6 +611,7 @@ def run_gpu(args, w):
                        "solver": f"odd-even GMRES({w['restart']}) FP32 inner solves in FP64 iterative refinement, "
                                  f"tol {w['tol']}",
                        "basis_storage": args.precision,
+                       "gram_schmidt": {0: "CGS1", 1: "CGS2", 2: "delayed CGS2"}.get(results[0].ortho, "?"),
                        "parallelism": f"rhs batches, {world} independent rank(s)",
                        "l2": "working set (basis 33 x %.0f MB) far above the 129 MB L2" %
                              ((V // 2) * 12 * nrhs * 8 / 1e6)},
@@ -720,6 +729,8 @@ def main():
                     help="inner Arnoldi basis storage of the timed solve (FP32 arithmetic either way)")
     ap.add_argument("--nvec", type=int, default=None,
                     help="ortho workload: basis size of the timed CGS2 step (default 16)")
+    ap.add_argument("--reorth", type=int, default=2, choices=[0, 1, 2],
+                    help="solve workloads: Gram-Schmidt of the Arnoldi step (0 CGS1, 1 CGS2, 2 delayed CGS2)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
     args = ap.parse_args()

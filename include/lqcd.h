@@ -218,7 +218,7 @@ typedef struct {
                          re-orthogonalisation delayed by one step, two passes per step
                          (C64 / BF16S with restart_len <= 32 where the streaming
                          Gram-Schmidt kernel takes the block: nrhs <= 32, or even
-                         nrhs <= 64 with C64; else as 1).
+                         nrhs <= 64; else as 1).
                          A BF16 basis
                          always re-orthogonalises (0 acts as 1) */
   int profile;        /* 1: time operator and Gram-Schmidt launches with CUDA events

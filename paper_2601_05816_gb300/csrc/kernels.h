@@ -63,7 +63,7 @@ bool gs_stream_passes_supported_bf16(const BlasPlan& plan, int64_t n, int nvec_m
 // [plan.blocks][nvec + 1][nrhs]. skip: optional device flag (return when set).
 //   oscale: optional device double [nrhs]; the updated w is multiplied by it before the store
 //   (dots and norm refer to the unscaled w). With neither dots nor norm no reduction runs.
-//   basis_bf16: basis stored as BF16 pairs (FP32 arithmetic, w in FP32; needs nrhs <= 32);
+//   basis_bf16: basis stored as BF16 pairs (FP32 arithmetic, w in FP32; needs plan.split);
 //   wout: optional, the scaled updated w is stored there (in the basis storage type) instead of in w.
 cudaError_t launch_gs_pass(bool f64, const BlasPlan& plan, int64_t n, int nvec, const void* basis,
                            int64_t vstride, void* w, const void* coef, bool update, bool dots,

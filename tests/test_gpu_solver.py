@@ -263,5 +263,32 @@ def test_gram_schmidt_modes_agree(precision, op):
         rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
         assert np.all(rel <= 1e-10), (reorth, rel)
         its[reorth] = res.iterations
+        assert res.ortho == reorth, (reorth, res.ortho)
     assert abs(its[2] - its[1]) <= max(4, its[1] // 10), its
+    lat.close()
+
+
+@pytest.mark.gpu
+def test_delayed_gram_schmidt_selection():
+    """reorth = 2 runs the delayed CGS2 where its kernels apply (FP32 / BF16 basis, restart length <= 32,
+    nrhs <= 32 or even nrhs <= 64) and CGS2 otherwise; every case converges."""
+    dims = (4, 4, 4, 4)
+    m0, c_sw = 0.1, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1201)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    cases = [  # (nrhs, precision, restart_len, expected Gram-Schmidt)
+        (4, lq.C64, 32, 2), (4, lq.BF16S, 32, 2), (40, lq.C64, 16, 2), (33, lq.C64, 16, 1),
+        (40, lq.BF16S, 16, 2), (4, lq.C64, 40, 1), (4, lq.C128, 16, 1), (3, lq.C64, 1, 2)]
+    for nrhs, prec, m, expect in cases:
+        b = syn.gaussian_spinors(dims, nrhs, 1202 + nrhs)
+        x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+        res = lat.solve(torch.from_numpy(b).cuda(), x, nrhs, op=lq.OP_SCHUR, precision=prec, restart_len=m,
+                        tol=1e-9, max_restarts=2000, reorth=2)
+        torch.cuda.synchronize()
+        assert res.status == lq.OK, (nrhs, prec, m, res)
+        assert res.ortho == expect, (nrhs, prec, m, res.ortho)
+        rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
+        assert np.all(rel <= 1e-9), (nrhs, prec, m, rel.max())
     lat.close()
