@@ -150,8 +150,13 @@ __host__ __device__ constexpr bool two_ctas(int nv, int epl) { return nv * epl <
 
 // NV: the largest nvec of the instance (8, 16, 24 or 32): the dot accumulators
 // a_i live in registers, NV * EPL complex per thread.
-template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM>
+// VSPLIT (update + dots, one rhs per lane, two rows per warp): the two half-warps split the
+// vectors (i even / odd) instead of the rows; each handles its vectors for both rows of the
+// warp and the update's partial sums and the updated w are exchanged with the partner lane
+// by one shuffle. Half the dot accumulators, and room for the coefficients in registers.
+template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM, bool VSPLIT = false>
 __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream_kernel(const Args a) {
+  static_assert(!VSPLIT || (UPDATE && DOTS && EPL == 1 && NV % 2 == 0), "vector split: update + dots, EPL 1");
   using C = float2;
   if (a.skip != nullptr && *a.skip != 0) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -189,14 +194,15 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
     }
   __syncthreads();
 
-  float ar[NV][EPL], ai[NV][EPL];
+  constexpr int NA = VSPLIT ? NV / 2 : NV;  // dot accumulators per lane
+  float ar[NA][EPL], ai[NA][EPL];
   float nn[EPL], sc[EPL];
 #pragma unroll
   for (int q = 0; q < EPL; ++q) {
     nn[q] = 0.f;
     sc[q] = (UPDATE && a.oscale != nullptr && lane_on && warp < kConsumers) ? (float)a.oscale[r + q] : 1.f;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) { ar[i][q] = 0.f; ai[i][q] = 0.f; }
+    for (int i = 0; i < NA; ++i) { ar[i][q] = 0.f; ai[i][q] = 0.f; }
   }
 
   if (warp == kConsumers) {
@@ -237,11 +243,16 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
     // with one rhs per lane the lane's update coefficients are the same for every element
     // it visits: kept in registers (one shared-memory read per basis element fewer) where
     // the instance has the registers to spare (the 16- and 32-vector ones would spill)
-    constexpr bool kCoefRegs = UPDATE && EPL == 1 && (NV == 8 || NV == 24);
-    C cr[kCoefRegs ? NV : 1];
+    constexpr bool kCoefRegs = UPDATE && EPL == 1 && (NV == 8 || NV == 24 || VSPLIT);
+    constexpr int NC = kCoefRegs ? NA : 1;
+    C cr[NC];  // VSPLIT: the coefficients of vectors 2k + hrow
 #pragma unroll
-    for (int i = 0; i < (kCoefRegs ? NV : 1); ++i)
-      cr[i] = (kCoefRegs && i < nvec && lane_on) ? cs[i * nrhs + r] : make_float2(0.f, 0.f);
+    for (int k = 0; k < NC; ++k) {
+      const int i = VSPLIT ? 2 * k + hrow : k;
+      cr[k] = (kCoefRegs && i < nvec && lane_on) ? cs[i * nrhs + r] : make_float2(0.f, 0.f);
+    }
+    // VSPLIT: the lane holding the same rhs in the other row of the warp's row pair
+    const int partner = (VSPLIT && lane_on) ? (hrow == 0 ? lane + lpr : lane - lpr) : lane;
     for (int l = 0; l < L; ++l) {
       const int s = l % S;
       if (!mbar_wait_bounded(&full[s], (uint32_t)(l / S) & 1u)) {
@@ -254,6 +265,65 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
       const unsigned char* st = stages + (size_t)s * a.stage_bytes;
       const B* vt = reinterpret_cast<const B*>(st);
       const C* wt = reinterpret_cast<const C*>(st + (size_t)nvec * a.vt_bytes);
+      if constexpr (VSPLIT) {
+        for (int j = 0; j < J; ++j) {
+          const int rowA = (j * kConsumers + warp) * 2;  // H == 2: the warp's rows rowA, rowA + 1
+          if (rowA >= rows) continue;                     // warp-uniform
+          const bool okB = rowA + 1 < rows;
+          const bool mine_ok = lane_on && (hrow == 0 || okB);
+          const int eA = rowA * nrhs + r, eB = eA + nrhs;
+          const int e = hrow == 0 ? eA : eB;
+          C wn = mine_ok ? wt[e] : make_float2(0.f, 0.f);
+          // partial update sums over this lane's vectors, for both rows (two chains each)
+          C sa[2], sb[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) { sa[u] = make_float2(0.f, 0.f); sb[u] = make_float2(0.f, 0.f); }
+#pragma unroll
+          for (int k = 0; k < NA; ++k) {
+            const int i = 2 * k + hrow;
+            if (lane_on && i < nvec) {
+              C va[1], vb[1] = {make_float2(0.f, 0.f)};
+              lds<1>(vt + (size_t)i * vte + eA, va);
+              if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
+              const C c = cr[k];
+              sa[k & 1].x += c.x * va[0].x - c.y * va[0].y;
+              sa[k & 1].y += c.x * va[0].y + c.y * va[0].x;
+              sb[k & 1].x += c.x * vb[0].x - c.y * vb[0].y;
+              sb[k & 1].y += c.x * vb[0].y + c.y * vb[0].x;
+            }
+          }
+          const C pa = make_float2(sa[0].x + sa[1].x, sa[0].y + sa[1].y);
+          const C pb = make_float2(sb[0].x + sb[1].x, sb[0].y + sb[1].y);
+          const C mine = hrow == 0 ? pa : pb, other = hrow == 0 ? pb : pa;
+          // the partner's partial for this lane's row (the partner sends its sum for the other row)
+          const float ox = __shfl_sync(0xffffffffu, other.x, partner);
+          const float oy = __shfl_sync(0xffffffffu, other.y, partner);
+          wn = make_float2(wn.x - (mine.x + ox), wn.y - (mine.y + oy));
+          if (mine_ok) {
+            const C ws[1] = {make_float2(wn.x * sc[0], wn.y * sc[0])};
+            if (a.wout != nullptr) stg<1>((B*)a.wout + row0 * nrhs + e, ws);
+            else stg<1>(w + row0 * nrhs + e, ws);
+            if (NORM) nn[0] += wn.x * wn.x + wn.y * wn.y;
+          }
+          // dots of this lane's vectors with the updated w of both rows
+          const float wx = __shfl_sync(0xffffffffu, wn.x, partner);
+          const float wy = __shfl_sync(0xffffffffu, wn.y, partner);
+          C wa = hrow == 0 ? wn : make_float2(wx, wy);
+          C wb = hrow == 0 ? make_float2(wx, wy) : wn;
+          if (!okB) wb = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < NA; ++k) {
+            const int i = 2 * k + hrow;
+            if (lane_on && i < nvec) {
+              C va[1], vb[1] = {make_float2(0.f, 0.f)};
+              lds<1>(vt + (size_t)i * vte + eA, va);
+              if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
+              ar[k][0] += (va[0].x * wa.x + va[0].y * wa.y) + (vb[0].x * wb.x + vb[0].y * wb.y);
+              ai[k][0] += (va[0].x * wa.y - va[0].y * wa.x) + (vb[0].x * wb.y - vb[0].y * wb.x);
+            }
+          }
+        }
+      } else
       for (int j = 0; j < J; ++j) {
         const int row = (j * kConsumers + warp) * H + hrow;
         if (!(lane_on && row < rows)) continue;
@@ -275,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               lds<EPL>(vt + (size_t)i * vte + e, v);
 #pragma unroll
               for (int q = 0; q < EPL; ++q) {
-                const C c = kCoefRegs ? cr[i] : cs[i * nrhs + r + q];
+                const C c = kCoefRegs ? cr[i < NC ? i : 0] : cs[i * nrhs + r + q];
                 pr[i & 3][q] += c.x * v[q].x - c.y * v[q].y;
                 pi[i & 3][q] += c.x * v[q].y + c.y * v[q].x;
               }
@@ -329,9 +399,19 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
       for (int i = 0; i < NV; ++i)
         if (i >= i0 && i < i0 + RV && i < nvec)
 #pragma unroll
-          for (int q = 0; q < EPL; ++q)
+          for (int q = 0; q < EPL; ++q) {
+            float vr, vi;
+            if constexpr (VSPLIT) {  // vector i sits in the lanes of row group i & 1
+              const bool own = (i & 1) == hrow;
+              vr = own ? ar[i >> 1][q] : 0.f;
+              vi = own ? ai[i >> 1][q] : 0.f;
+            } else {
+              vr = ar[i][q];
+              vi = ai[i][q];
+            }
             red[(((i - i0) * kConsumers + warp) * EPL + q) * 32 + lane] =
-                make_double2(DOTS ? (double)ar[i][q] : 0.0, DOTS ? (double)ai[i][q] : 0.0);
+                make_double2(DOTS ? (double)vr : 0.0, DOTS ? (double)vi : 0.0);
+          }
     }
     __syncthreads();
     for (int t2 = tid; t2 < RV * nrhs; t2 += kThreads) {

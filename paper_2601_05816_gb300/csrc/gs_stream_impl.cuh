@@ -6,9 +6,9 @@
 namespace lqcd {
 namespace gss {
 
-template <typename B, int EPL, int NV, bool U, bool D, bool N>
+template <typename B, int EPL, int NV, bool U, bool D, bool N, bool VS = false>
 static cudaError_t launch_one(const Plan& p, int blocks, const Args& a, cudaStream_t s) {
-  auto k = gs_stream_kernel<B, EPL, NV, U, D, N>;
+  auto k = gs_stream_kernel<B, EPL, NV, U, D, N, VS>;
   // allow the largest layout make_plan can choose, once per device
   static unsigned configured = 0;
   int dev = 0;
@@ -29,6 +29,13 @@ static cudaError_t launch_one(const Plan& p, int blocks, const Args& a, cudaStre
 template <typename B, int EPL, int NV>
 static cudaError_t launch_flags(bool up, bool dots, bool norm, const Plan& p, int blocks, const Args& a,
                                 cudaStream_t s) {
+  // update + dots with two rows per warp and 17-32 vectors: the vector-split consumers
+  if constexpr (EPL == 1 && NV >= 24) {
+    if (up && dots && p.H == 2) {
+      if (norm) return launch_one<B, EPL, NV, true, true, true, true>(p, blocks, a, s);
+      return launch_one<B, EPL, NV, true, true, false, true>(p, blocks, a, s);
+    }
+  }
   if (up && dots && norm) return launch_one<B, EPL, NV, true, true, true>(p, blocks, a, s);
   if (!up && dots && norm) return launch_one<B, EPL, NV, false, true, true>(p, blocks, a, s);
   if (up && dots) return launch_one<B, EPL, NV, true, true, false>(p, blocks, a, s);
