@@ -69,8 +69,8 @@ WORKLOADS = {
 # precision, Gram-Schmidt variant); the summaries are under profiles/. The reported traffic
 # per step is the timed solve's algorithmic bytes per step times their ratio (the timed
 # steps have a different mix of basis sizes than one full cycle). Cases not captured: null.
-GS_DRAM_CAPTURE = {("solve", "c64", 2): (115.67273088e9, 1152 * 100663296.0),
-                   ("solve", "bf16", 2): (60.980819968e9, 1216 * 50331648.0)}
+GS_DRAM_CAPTURE = {("solve", "c64", 2): (115.670896896e9, 1152 * 100663296.0),
+                   ("solve", "bf16", 2): (60.98132736e9, 1216 * 50331648.0)}
 
 
 def measured_peaks():
