@@ -8,10 +8,12 @@ residual with the FP32 operator and Arnoldi process in inner solves of an FP64
 iterative refinement (the solve's last step applies the full FP64 operator to
 report the final residual).
 
-Workloads (synthetic, seeded; see the design doc for the recipe):
+Workloads (synthetic and seeded: gauge links exp(i eps H) with H a Gaussian su(3) element per
+link, Gaussian sources; the generators are in synthetic/):
   solve        16^3 x 32, Wilson-clover c_sw = 1, U = exp(i 0.3 H), m0 = -0.2,
                nrhs = 16 Gaussian sources (the operator-sweep lattice)   [default]
   solve-large  32^3 x 64, U = exp(i 0.25 H), m0 = -0.3, nrhs = 12
+  batch, adjoint, apply, ortho: see WORKLOADS below
 
 value = sites x rhs solved per second, summed over ranks (each rank solves its
 own batch: weak scaling, no communication). The JSON line also reports the
