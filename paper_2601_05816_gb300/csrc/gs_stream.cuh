@@ -1,9 +1,9 @@
 // Streaming Gram-Schmidt pass: warp-specialised, basis tiles staged in shared
 // memory by bulk asynchronous copies (cp.async.bulk, completion on mbarriers).
 //
-// The pass is the one of Algorithm 2's orthogonalisation step (classical
-// Gram-Schmidt with one re-orthogonalisation, Sec. III-B-2) on a block of nrhs
-// systems stored rhs-innermost. A tile is a range of whole rows of nrhs
+// The pass is one pass of the orthogonalisation in Algorithm 2's Arnoldi step
+// (Sec. III-A-2), done as classical Gram-Schmidt with re-orthogonalisation (CGS2,
+// or the solver's delayed CGS2), on a block of nrhs systems stored rhs-innermost. A tile is a range of whole rows of nrhs
 // elements, so the tile of basis vector i is one contiguous range of memory and
 // one bulk copy per vector (plus one for w) fills a pipeline stage. The bytes in
 // flight are set by the stage count and size, not by registers or occupancy.
@@ -16,7 +16,10 @@
 //   a_i += conj(v_i) w'                 (dots, per thread and vector, in registers)
 //   n   += |w'|^2                       (norm)
 // need no exchange between warps: there is no block-wide barrier per tile, a warp
-// releases a stage with one mbarrier arrival. The per-(vector, rhs) sums over
+// releases a stage with one mbarrier arrival. (The vector-split instance for
+// update + dots with 17-32 vectors and two rows per warp is the exception inside a
+// warp: its two half-warps own the even / odd vectors of both rows and exchange
+// partial sums by shuffles.) The per-(vector, rhs) sums over
 // lanes and warps, and the norm, go to per-CTA partials in a fixed order at the
 // end (deterministic, like every reduction here).
 #pragma once
