@@ -729,6 +729,8 @@ def main():
     ap.add_argument("--max-restarts", type=int, default=500)
     ap.add_argument("--precision", default="c64", choices=["c64", "bf16"],
                     help="inner Arnoldi basis storage of the timed solve (FP32 arithmetic either way)")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="apply / ortho workloads: number of rhs (default 16)")
     ap.add_argument("--nvec", type=int, default=None,
                     help="ortho workload: basis size of the timed CGS2 step (default 16)")
     ap.add_argument("--reorth", type=int, default=2, choices=[0, 1, 2],
@@ -741,6 +743,9 @@ def main():
         w["m0_prescribed"] = w["m0"]
         w["m0"] = args.m0
         w["name"] += f" (companion run, m0 {args.m0} instead of {w['m0_prescribed']})"
+    if args.nrhs is not None and w.get("kind") in ("apply", "ortho"):
+        w["name"] = w["name"].replace(f"nrhs={w['nrhs']}", f"nrhs={args.nrhs}")
+        w["nrhs"] = args.nrhs
     if args.nvec is not None and w.get("kind") == "ortho":
         w["name"] = w["name"].replace(f"nvec={w['nvec']}", f"nvec={args.nvec}")
         w["nvec"] = args.nvec

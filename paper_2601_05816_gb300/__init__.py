@@ -248,7 +248,7 @@ class Lattice:
 
     def tune(self, dtype: int, nrhs: int, reps: int = 5, stream=None):
         """Autotune the hopping-kernel variant for (dtype, nrhs); returns [(full_ms, schur_ms)] per variant."""
-        times = (ctypes.c_double * 64)()
+        times = (ctypes.c_double * 256)()
         n = ctypes.c_int(0)
         _check(self._lib.lqcd_tune(self._h, int(dtype), int(nrhs), int(reps), times, ctypes.byref(n),
                                    _stream(stream)), "lqcd_tune")

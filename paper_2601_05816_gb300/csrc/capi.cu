@@ -116,6 +116,7 @@ static DslashArgs<Real> base_args(lqcd_ctx ctx, int nrhs, bool f64) {
   a.links = (const typename Cplx<Real>::T*)(f64 ? ctx->links64 : ctx->links32);
   a.blocks = (const Real*)(f64 ? ctx->blk64 : ctx->blk32);
   a.blocks_inv = (const Real*)(f64 ? ctx->inv64 : ctx->inv32);
+  a.num_sms = ctx->num_sms;
   return a;
 }
 

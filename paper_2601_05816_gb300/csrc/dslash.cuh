@@ -26,6 +26,9 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace lqcd {
@@ -52,6 +55,7 @@ struct DslashArgs {
   Real self_scalar, post_scalar, c_hop;
   const int* skip;     // optional: return at once when *skip != 0
   int loop_chunk;      // persistent variants: target sites per CTA (set by the launcher)
+  int num_sms;         // SMs of the context's device (persistent variants size their grid by it)
 };
 
 // NR complex numbers (NR consecutive rhs of one component).
@@ -260,6 +264,52 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
   hop_compute<Real, NR, MU, DIR>(u, up, dn, acc);
 }
 
+// L1 prefetch of one hopping direction's operands (the neighbour spinor of this
+// site and its link), issued PF directions ahead of their loads in the variants
+// compiled for a fixed rhs count (site tile of one site, so a site's spinor is one
+// contiguous run of 12 * NRHS complex numbers). The site's NRHS / NR lanes split
+// the run's 128-byte lines between them. A prefetch holds no register, so the
+// bytes in flight per warp are no longer bounded by the registers that receive
+// them; the later loads of that direction then hit L1.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+template <typename Real, int NR, int MU, int DIR, typename HIN, int NRHS>
+__device__ __forceinline__ void prefetch_dir(const DslashArgs<Real>& a, const Coord& c, int p, const HIN* hin) {
+  static_assert(NRHS >= 16, "prefetch variants need a site tile of one site");
+  constexpr int G = NRHS / NR;                                  // lanes of one site
+  constexpr int LINES = 12 * NRHS * (int)sizeof(HIN) / 128;     // lines of one site's spinor
+  const int ncb = neighbour_lex<MU, DIR>(a.g, c) >> 1;
+  const char* sp = reinterpret_cast<const char*>(hin + (int64_t)ncb * 12 * NRHS);
+#pragma unroll
+  for (int l = 0; l < (LINES + G - 1) / G; ++l) {
+    const int line = (int)threadIdx.x + l * G;
+    if (line < LINES) prefetch_l1(sp + line * 128);
+  }
+  const int link_site = (DIR > 0) ? (p * a.g.Vh + (c.lex >> 1)) : ((1 - p) * a.g.Vh + ncb);
+  const typename Cplx<Real>::T* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
+#pragma unroll
+  for (int l = 0; l < (9 + G - 1) / G; ++l) {
+    const int e = (int)threadIdx.x + l * G;
+    if (e < 9) prefetch_l1(lp + (int64_t)e * a.g.V);
+  }
+}
+
+// Direction K = 0..7 of the hopping sum: mu = K / 2, forward for even K.
+template <int K> struct DirOf {
+  static constexpr int MU = K / 2;
+  static constexpr int DIR = (K % 2 == 0) ? +1 : -1;
+};
+
+template <typename Real, int NR, bool BATCH, typename HIN, int NRHS, int PF, int K>
+__device__ __forceinline__ void hop_step(const DslashArgs<Real>& a, const Coord& c, int p, int r0, const HIN* hin,
+                                         MC<Real, NR> acc[12]) {
+  if constexpr (PF > 0 && K + PF < 8)
+    prefetch_dir<Real, NR, DirOf<K + PF>::MU, DirOf<K + PF>::DIR, HIN, NRHS>(a, c, p, hin);
+  hop_dir<Real, NR, DirOf<K>::MU, DirOf<K>::DIR, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+}
+
 // Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 strictly
 // lower entries L(l, j), l > j, in the order (1,0), (2,0), (2,1), (3,0), ...
 // (index l(l-1)/2 + j) as (re, im) pairs: 36 reals. Site blocks hold the upper
@@ -323,7 +373,7 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
 }
 
 // The whole operator on one target site for this thread's NR rhs.
-template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0>
+template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0, int PF = 0>
 __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site) {
   using C = typename Cplx<Real>::T;
   const int r0 = threadIdx.x * NR;
@@ -344,14 +394,18 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
   if (a.hop) {
     const Coord c = site_coords(a.g, p, cb);
     const HIN* hin = reinterpret_cast<const HIN*>(a.hop_in) + (a.full ? (1 - p) * a.half_elems : 0);
-    hop_dir<Real, NR, 0, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 0, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 1, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 2, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, +1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
-    hop_dir<Real, NR, 3, -1, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+    if constexpr (PF > 0) {
+      prefetch_dir<Real, NR, 0, +1, HIN, NRHS>(a, c, p, hin);
+      if constexpr (PF > 1) prefetch_dir<Real, NR, 0, -1, HIN, NRHS>(a, c, p, hin);
+    }
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 0>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 1>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 2>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 3>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 4>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 5>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 6>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 7>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -401,12 +455,12 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
 }
 
 template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0>
+          typename SIN, int NRHS = 0, int PF = 0>
 __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   if (a.skip != nullptr && *a.skip != 0) return;
   if (!LOOP) {
     const int site = blockIdx.x * blockDim.y + threadIdx.y;
-    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS>(a, site);
+    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF>(a, site);
     return;
   }
   // persistent CTAs: each walks one contiguous chunk of target sites, blockDim.y
@@ -415,7 +469,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   const int s0 = blockIdx.x * a.loop_chunk;
   const int s1 = min(s0 + a.loop_chunk, a.n_target);
   for (int site = s0 + threadIdx.y; site < s1; site += blockDim.y)
-    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS>(a, site);
+    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF>(a, site);
 }
 
 // Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
@@ -428,6 +482,7 @@ struct DslashVariant {
   int batch;   // direct loads: 1 = each direction's loads issued as one batch
   int loop;    // direct loads: 1 = persistent CTAs walking contiguous chunks of sites
   int nrhs_fixed = 0;  // > 0: compiled for this rhs count only (immediate component offsets)
+  int prefetch = 0;    // with nrhs_fixed: L1 prefetch of the operands this many directions ahead
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -440,21 +495,27 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
 template <typename Real, int NR, int SM, int PM, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0>
+          typename SIN, int NRHS = 0, int PF = 0>
 cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
-  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS>;
+  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF>;
   dim3 grid((a.n_target + block.y - 1) / block.y);
+  if (PF > 0) {
+    // the prefetched lines live in L1: ask for the smallest shared-memory carve-out
+    static std::once_flag carveout;
+    std::call_once(carveout, [&] { cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0); });
+  }
   if (LOOP) {
-    // one wave of persistent CTAs, each with an equal contiguous chunk of sites
-    static int per_sm = 0, sms = 0;
+    // one wave of persistent CTAs, each with an equal contiguous chunk of sites; the
+    // resident-CTA count depends only on the kernel and the architecture, the SM count
+    // comes from the context's device
+    static std::atomic<int> per_sm_cache{0};
+    int per_sm = per_sm_cache.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block.x * block.y, 0);
       if (per_sm < 1) per_sm = 1;
+      per_sm_cache.store(per_sm, std::memory_order_relaxed);
     }
-    const int want = sms * per_sm;
+    const int want = (a.num_sms > 0 ? a.num_sms : 1) * per_sm;
     const int rows = (int)grid.x;
     const int per_cta = (rows + want - 1) / want;
     a.loop_chunk = per_cta * (int)block.y;
@@ -465,12 +526,13 @@ cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
 }
 
 template <typename Real, int NR, int MAXT, int MINB, bool BATCH, bool LOOP = false,
-          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0>
+          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0, int PF = 0>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
   if (NRHS > 0 && (a.lay.nrhs != NRHS || a.lay.log_s != 0)) return cudaErrorInvalidValue;
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
-#define LQCD_DS(SM, PM) return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS>(a, block, s)
+#define LQCD_DS(SM, PM) \
+  return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF>(a, block, s)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -486,9 +548,9 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
 #define LQCD_DSLASH_VARIANT_TU(REAL, NR, MAXT, MINB, BATCH, LOOP) \
   template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, BATCH, LOOP>(const DslashArgs<REAL>&, int, int, cudaStream_t);
 // ... and of a variant with the rhs count fixed at compile time.
-#define LQCD_DSLASH_VARIANT_NRHS_TU(REAL, NR, MAXT, MINB, NRHS)                                            \
+#define LQCD_DSLASH_VARIANT_NRHS_TU(REAL, NR, MAXT, MINB, NRHS, PF)                                        \
   template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, false, false, typename Cplx<REAL>::T, \
-                                             typename Cplx<REAL>::T, NRHS>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+                                             typename Cplx<REAL>::T, NRHS, PF>(const DslashArgs<REAL>&, int, int, cudaStream_t);
 
 // FP32 arithmetic on BF16-stored inputs (hop input HIN, self-term input SIN), FP32 output.
 cudaError_t launch_dslash_bf16(const DslashArgs<float>& a, int self_mode, int post_mode, bool hop_bf16,

@@ -5,9 +5,12 @@ namespace lqcd {
 
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
-//  batched loads, persistent chunk loop}
+//  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance}
 const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
-                             {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16}};
+                             {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16},
+                             {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
+                             {2, 128, 4, 0, 0, 0, 32}, {2, 128, 4, 0, 0, 0, 32, 1},
+                             {2, 128, 4, 0, 0, 0, 64}, {2, 128, 4, 0, 0, 0, 64, 1}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -24,8 +27,19 @@ extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, true>
 extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, true, true>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<float, 1, 128, 6, false, true>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16>(const DslashArgs<float>&, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16>(const DslashArgs<float>&, int, int, cudaStream_t);
+#define LQCD_EXTERN_NRHS(MAXT, MINB, NRHS, PF)                                                             \
+  extern template cudaError_t launch_dslash_variant<float, 2, MAXT, MINB, false, false, float2, float2, NRHS, PF>( \
+      const DslashArgs<float>&, int, int, cudaStream_t);
+LQCD_EXTERN_NRHS(128, 4, 16, 0)
+LQCD_EXTERN_NRHS(256, 2, 16, 0)
+LQCD_EXTERN_NRHS(128, 4, 16, 1)
+LQCD_EXTERN_NRHS(128, 4, 16, 2)
+LQCD_EXTERN_NRHS(256, 2, 16, 1)
+LQCD_EXTERN_NRHS(128, 4, 32, 0)
+LQCD_EXTERN_NRHS(128, 4, 32, 1)
+LQCD_EXTERN_NRHS(128, 4, 64, 0)
+LQCD_EXTERN_NRHS(128, 4, 64, 1)
+#undef LQCD_EXTERN_NRHS
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
@@ -69,8 +83,18 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
     case 10: return launch_dslash_variant<float, 2, 128, 4, true, true>(a, self_mode, post_mode, s);
     case 11: return launch_dslash_variant<float, 2, 256, 2, false, true>(a, self_mode, post_mode, s);
     case 12: return launch_dslash_variant<float, 1, 128, 6, false, true>(a, self_mode, post_mode, s);
-    case 13: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16>(a, self_mode, post_mode, s);
-    case 14: return launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16>(a, self_mode, post_mode, s);
+#define LQCD_CASE_NRHS(IDX, MAXT, MINB, NRHS, PF) \
+  case IDX: return launch_dslash_variant<float, 2, MAXT, MINB, false, false, float2, float2, NRHS, PF>(a, self_mode, post_mode, s);
+    LQCD_CASE_NRHS(13, 128, 4, 16, 0)
+    LQCD_CASE_NRHS(14, 256, 2, 16, 0)
+    LQCD_CASE_NRHS(15, 128, 4, 16, 1)
+    LQCD_CASE_NRHS(16, 128, 4, 16, 2)
+    LQCD_CASE_NRHS(17, 256, 2, 16, 1)
+    LQCD_CASE_NRHS(18, 128, 4, 32, 0)
+    LQCD_CASE_NRHS(19, 128, 4, 32, 1)
+    LQCD_CASE_NRHS(20, 128, 4, 64, 0)
+    LQCD_CASE_NRHS(21, 128, 4, 64, 1)
+#undef LQCD_CASE_NRHS
     default: return cudaErrorInvalidValue;
   }
 }

@@ -2,5 +2,5 @@
 #include "dslash.cuh"
 
 namespace lqcd {
-LQCD_DSLASH_VARIANT_NRHS_TU(float, 2, 128, 4, 16)
+LQCD_DSLASH_VARIANT_NRHS_TU(float, 2, 128, 4, 16, 0)
 }  // namespace lqcd

@@ -1,0 +1,6 @@
+// FP32 hopping-kernel variant 20: 2 rhs per thread, 128 threads, >= 4 CTAs/SM, compiled for 64 rhs.
+#include "dslash.cuh"
+
+namespace lqcd {
+LQCD_DSLASH_VARIANT_NRHS_TU(float, 2, 128, 4, 64, 0)
+}  // namespace lqcd

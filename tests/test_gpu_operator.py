@@ -214,15 +214,18 @@ def test_orthogonalise_matches_projection(dtype, nvec, nrhs, reorth):
 
 
 @pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
-def test_operator_sweep_lattice_sampled_rhs(dtype):
-    """16^3 x 32, Wilson-clover, nrhs = 16 in the launch configuration the bench
-    times; rhs 0 and 15 checked against the oracle (rhs are independent)."""
+@pytest.mark.parametrize("nrhs", [16, 64])
+def test_operator_sweep_lattice_sampled_rhs(dtype, nrhs):
+    """16^3 x 32, Wilson-clover, nrhs = 16 and 64 in the launch configuration the bench's operator
+    sweep times (the autotuner's choice for that nrhs); the first and last rhs checked against the
+    oracle (rhs are independent)."""
     dims = (32, 16, 16, 16)
-    m0, c_sw, nrhs = -0.2, 1.0, 16
+    m0, c_sw = -0.2, 1.0
     U = syn.gauge_field(dims, "exp", 0.3, seed=1 * 1000 + 1)
     lat = lq.Lattice(dims, time_bc=-1)
     lat.set_gauge(torch.from_numpy(U).cuda())
     lat.set_clover(m0, c_sw)
+    lat.tune(dtype, nrhs, reps=2)
     psi = syn.gaussian_spinors(dims, nrhs, 1 * 1000 + 2)
     psi_o = oracle.split_parity(psi, 1)
     sample = [0, nrhs - 1]
@@ -239,8 +242,108 @@ def test_operator_sweep_lattice_sampled_rhs(dtype):
         lat.unpack(sites, nrhs, pout, out)
         torch.cuda.synchronize()
         got = out.cpu().numpy()[sample]
-        assert relerr(got, ref) < TOL[dtype]
+        assert relerr(got, ref) < TOL[dtype], (op, lat.kernel_variant(dtype, nrhs, op))
     lat.close()
+
+
+def _sample_sites(dims, parity, n, seed):
+    """n sites of the given parity: the lattice corners and both time boundaries, then random ones."""
+    rng = np.random.default_rng(seed)
+    T, Z, Y, X = dims
+    fixed = [(0, 0, 0, 1), (T - 1, Z - 1, Y - 1, X - 2), (T - 1, 0, 0, 0), (0, Z - 1, Y - 1, X - 1),
+             (T - 1, Z - 1, 0, 1), (0, 0, Y - 1, 0)]
+    out = [x for x in fixed if sum(x) % 2 == parity]
+    while len(out) < n:
+        x = tuple(int(rng.integers(0, d)) for d in dims)
+        if sum(x) % 2 == parity and x not in out:
+            out.append(x)
+    return out
+
+
+_LARGE = {}
+
+
+def _large_inputs(dims, nrhs):
+    """Gauge field and sources of the 32^3 x 64 workload (generated once per module: ~2 minutes)."""
+    if dims not in _LARGE:
+        _LARGE.clear()
+        _LARGE[dims] = (syn.gauge_field(dims, "exp", 0.25, seed=2 * 1000 + 0),
+                        syn.gaussian_spinors(dims, nrhs, 2 * 1000 + 1))
+    return _LARGE[dims]
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+def test_operator_32x64_lattice_sampled_sites(dtype):
+    """The 32^3 x 64 Wilson-clover lattice of the large GMRES workload (eps 0.25, m0 = -0.3, 12 rhs),
+    2.1 M sites, in the tuned launch configuration: Schur and full applies at sampled sites (corners, both
+    time boundaries, random sites) and the first and last rhs, each output site computed one by one by the
+    per-site oracle. Rules out a size-dependent indexing fault (site numbers, packed offsets and link
+    offsets beyond 2^31 bytes)."""
+    from oracle import site
+    dims = (64, 32, 32, 32)
+    m0, c_sw, nrhs = -0.3, 1.0, 12
+    U, psi = _large_inputs(dims, nrhs)
+    lat = lq.Lattice(dims, time_bc=-1)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    lat.tune(dtype, nrhs, reps=1)
+    tol = 1e-12 if dtype == lq.C128 else 5e-6
+    # Schur operator on the odd sites
+    psi_o = oracle.split_parity(psi, 1)
+    d_in = dev(psi_o, dtype)
+    d_out = torch.empty_like(d_in)
+    lat.apply(lq.OP_SCHUR, nrhs, d_in, d_out)
+    got = d_out.cpu().numpy()
+    del d_in, d_out
+    for x in _sample_sites(dims, 1, 24, 5):
+        k = site.half_index(dims, x)
+        for r in (0, nrhs - 1):
+            ref = site.apply_schur_at(U, psi_o[r], x, m0, c_sw)
+            assert np.linalg.norm(got[r, k] - ref) <= tol * np.linalg.norm(ref), (x, r)
+    del psi_o, got
+    # full operator on all sites
+    d_in = dev(psi, dtype)
+    d_out = torch.empty_like(d_in)
+    lat.apply(lq.OP_FULL, nrhs, d_in, d_out)
+    got = d_out.cpu().numpy()
+    del d_in, d_out
+    for parity in (0, 1):
+        for x in _sample_sites(dims, parity, 12, 6 + parity):
+            for r in (0, nrhs - 1):
+                ref = site.apply_D_at(U, psi[r], x, m0, c_sw)
+                assert np.linalg.norm(got[(r,) + x] - ref) <= tol * np.linalg.norm(ref), (x, r)
+    lat.close()
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+@pytest.mark.parametrize("nrhs", [32, 64])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2]])
+def test_large_nrhs_every_kernel_variant(dtype, nrhs, case):
+    """nrhs 32 and 64 (two rhs per lane and the variants compiled for those counts): every launch
+    variant that fits, full and Schur operator, element-wise per rhs against the oracle."""
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    lib = lq.load()
+    psi = syn.gaussian_spinors(dims, nrhs, 700 + nrhs)
+    psi_o = oracle.split_parity(psi, 1)
+    ref_f = oracle.apply_D(U, psi, m0, C if c_sw else None)
+    ref_s = oracle.apply_schur(U, A, Ainv, psi_o)
+    ran = 0
+    for v in range(lib.lqcd_kernel_variant_count(dtype)):
+        for op, src, ref in ((lq.OP_FULL, psi, ref_f), (lq.OP_SCHUR, psi_o, ref_s)):
+            try:
+                lat.set_kernel_variant(dtype, nrhs, op, v)
+            except lq.LqcdError:
+                continue
+            d_in = dev(src, dtype)
+            d_out = torch.empty_like(d_in)
+            lat.apply(op, nrhs, d_in, d_out)
+            torch.cuda.synchronize()
+            assert relerr(d_out.cpu().numpy(), ref) < TOL[dtype], (v, op)
+            ran += 1
+    for op in (lq.OP_FULL, lq.OP_SCHUR):
+        lat.set_kernel_variant(dtype, nrhs, op, -1)
+    assert ran >= 4
 
 
 @pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
