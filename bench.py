@@ -33,6 +33,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 # the CPU oracle baseline is reported for one host thread
@@ -184,28 +186,70 @@ def aggregate_throughput(world: int, units_per_rank_step: float, steps: int, t_m
 
 # ------------------------------------------------------------------ oracle (CPU) arm
 
-def oracle_sample(w, iters: int):
-    """Time the FP64 numpy oracle's odd-even GMRES for `iters` Arnoldi steps on one rhs."""
-    import numpy as np
+def oracle_setup(w):
+    """Gauge field, site blocks and one Gaussian rhs of the workload for the FP64 numpy oracle."""
     import oracle
     import synthetic as syn
     U = syn.gauge_field(w["dims"], "exp", w["eps"], seed=w["gauge_seed"])
     b = syn.gaussian_spinors(w["dims"], 1, w["rhs_seed"])
     t0 = time.perf_counter()
     A, Ainv = oracle.diag_blocks(U, w["m0"], w["c_sw"])
-    t_setup = time.perf_counter() - t0
+    return U, A, Ainv, b, time.perf_counter() - t0
+
+
+def oracle_cycle(U, A, Ainv, b, m: int):
+    """One GMRES(m) cycle of the oracle's odd-even solve on one rhs, as the oracle stands:
+    source preparation, the initial residual, m Arnoldi steps, the update, the final
+    residual and the reconstruction (m + 2 Schur-operator applies)."""
+    import oracle
     t0 = time.perf_counter()
-    oracle.solve_eo(U, A, Ainv, b, tol=1e-30, m=iters, max_restarts=1)
-    t_cycle = time.perf_counter() - t0
-    del np
-    return t_setup, t_cycle
+    oracle.solve_eo(U, A, Ainv, b, tol=1e-30, m=m, max_restarts=1)
+    return time.perf_counter() - t0
+
+
+def oracle_apply_sample(w, nrhs: int):
+    """The FP64 oracle's Schur and full operator, each applied once to nrhs Gaussian rhs of the
+    workload's lattice, timed; returns site*rhs/s of each and the set-up time."""
+    import oracle
+    import synthetic as syn
+    U = syn.gauge_field(w["dims"], "exp", w["eps"], seed=w["gauge_seed"])
+    psi = syn.gaussian_spinors(w["dims"], nrhs, w["rhs_seed"] + 17)
+    t0 = time.perf_counter()
+    A, Ainv = oracle.diag_blocks(U, w["m0"], w["c_sw"])
+    t_setup = time.perf_counter() - t0
+    C = (4.0 + w["m0"]) * np.eye(12) - A          # C = (4 + m0) - A, no second clover build
+    psi_o = oracle.split_parity(psi, 1)
+    t0 = time.perf_counter()
+    oracle.apply_schur(U, A, Ainv, psi_o)
+    t_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.apply_D(U, psi, w["m0"], C)
+    t_f = time.perf_counter() - t0
+    V = psi.shape[1] * psi.shape[2] * psi.shape[3] * psi.shape[4]
+    return {"schur": V // 2 * nrhs / t_s, "full": V * nrhs / t_f, "schur_s": t_s, "full_s": t_f,
+            "setup_s": t_setup, "nrhs": nrhs}
 
 
 def cpu_threads():
     return int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
 
 
+def oracle_cost_model(U, A, Ainv, b, m, t_cycle_m):
+    """Cost of one Arnoldi step and of the fixed per-cycle work (preparation, residuals, update,
+    reconstruction) of the oracle's GMRES: one extra cycle of 2m steps, differenced with the
+    measured m-step cycle time."""
+    t2m = oracle_cycle(U, A, Ainv, b, 2 * m)
+    t_iter = max((t2m - t_cycle_m) / m, 1e-9)
+    return t_iter, max(t_cycle_m - m * t_iter, 0.0)
+
+
 def run_reference(args, w):
+    """The oracle arm: per step one GMRES(m) cycle of the oracle's odd-even solve on one rhs of the
+    workload (m = --ref-cycle-steps), timed as it stands; ms_per_step is that wall time. value
+    projects it to a whole solve in the GPU arm's unit (site*rhs solved per second): the oracle's
+    set-up (clover blocks) + the GPU solve's iteration count x the cost of one Arnoldi step + one
+    fixed per-cycle cost per GMRES(32) cycle, the step and fixed costs separated by one extra cycle
+    of 2m steps timed after the warm-up."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -215,22 +259,22 @@ def run_reference(args, w):
                           "the default workload times the oracle"}), flush=True)
         return
     V = w["dims"][0] * w["dims"][1] * w["dims"][2] * w["dims"][3]
-    # projected time to solution of one rhs: per-iteration oracle cost x the GPU solve's
-    # iteration count for this workload (fixed number recorded from the GPU run)
     its = args.ref_iterations
-    k = args.ref_sample_iters
+    m = args.ref_cycle_steps
+    U, A, Ainv, b, t_setup = oracle_setup(w)
     for _ in range(args.warmup):
-        oracle_sample(w, k)
-    times = []
-    for _ in range(args.steps):
-        ts, tc = oracle_sample(w, k)
-        times.append(ts + tc * its / k)
-    t = statistics.mean(times)
-    value = V * 1 / t
-    sample = (f"oracle odd-even GMRES, 1 rhs, {k} Arnoldi steps + set-up per step, projected to {its} "
-              f"iterations (the GPU solve's count)")
+        oracle_cycle(U, A, Ainv, b, m)
+    times = [oracle_cycle(U, A, Ainv, b, m) for _ in range(args.steps)]
+    t_step = statistics.mean(times)
+    t_iter, t_fixed = oracle_cost_model(U, A, Ainv, b, m, t_step)
+    cycles = -(-its // 32)
+    t_solve = t_setup + its * t_iter + cycles * t_fixed
+    value = V * 1 / t_solve
+    sample = (f"per step one oracle GMRES({m}) cycle of the odd-even solve on 1 rhs ({t_step:.2f} s); projected "
+              f"to one solve: set-up {t_setup:.1f} s + {its} Arnoldi steps x {t_iter:.2f} s + {cycles} cycles x "
+              f"{t_fixed:.2f} s fixed cost ({its} = the GPU solve's iterations per rhs)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site·rhs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": w["name"]},
             "cpu_baseline": {"value": value, "unit": "site·rhs/s", "cores": cpu_threads(), "kind": "oracle",
@@ -626,89 +670,230 @@ def run_gpu(args, w):
             "tuning": {"variant_ms_full_schur": tuning, "chosen_full_schur": chosen}}
 
     if rank == 0 and not args.skip_extras:
-        # operator sweep (dslash GB/s vs HBM roofline), L2 flushed between applies
-        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-        lat.set_gauge(U_d)
-        lat.set_clover(w["m0"], w["c_sw"])
-        sweep = []
-        nr_list = [int(v) for v in args.sweep.split(",")] if args.sweep else [1, 4, 16, 64]
-        for nr in nr_list:
-            for dt in (lq.C64, lq.C128):
-                for op in (lq.OP_SCHUR, lq.OP_FULL):
-                    if op == lq.OP_SCHUR:
-                        lat.tune(dt, nr, reps=3)
-                    tt, nb, units = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
-                    sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
-                                  "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
-                                  "variant": lat.kernel_variant(dt, nr, op),
-                                  "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
-                                  "site_rhs_per_s": units / tt})
-        del flush
-        line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48b+144)s/site, "
-                          "schur (120b+432)s/odd site", "l2_flush": "512 MB memset between applies",
-                          "points": sweep}
-        # FP64 plain GPU solve vs the mixed solve of the timed steps
-        torch.cuda.synchronize()
-        x_d.zero_()
-        t0 = time.perf_counter()
-        r64 = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=lq.C128, restart_len=w["restart"], tol=w["tol"],
-                        max_restarts=args.max_restarts, use_graph=True)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        mixed_s = statistics.mean(r.seconds for r in results)
-        x_d.zero_()
-        rg = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, profile=False))
-        torch.cuda.synchronize()
-        other = {}
-        for name, prec in (("c64", lq.C64), ("bf16", lq.BF16S)):
-            if prec == inner:
-                continue
-            x_d.zero_()
-            ro = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, precision=prec, profile=False))
-            torch.cuda.synchronize()
-            other[name] = {"seconds": ro.seconds, "iterations": ro.iterations, "restarts": ro.restarts,
-                           "fp64_residuals": ro.outer_steps, "relres": ro.relres_max}
-        line["gmres"] = {"fp64_s": t64, "mixed_s": mixed_s, "speedup": t64 / mixed_s,
-                         "fp64_iterations": r64.iterations, "mixed_iterations": results[-1].iterations,
-                         "fp64_relres": r64.relres_max, "mixed_relres": results[-1].relres_max,
-                         "mixed_graph_s": rg.seconds, "other_inner_storage": other,
-                         "note": "host wall time of one synchronised solve (step includes set_gauge/set_clover)"}
-        # end to end through the C ABI with pinned host buffers
-        U_h = torch.from_numpy(U).pin_memory()
-        b_h = torch.from_numpy(b).pin_memory()
-        x_h = torch.zeros_like(b_h).pin_memory()
-        lat.set_gauge(U_h.numpy())
-        lat.set_clover(w["m0"], w["c_sw"])
-        lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
-        torch.cuda.synchronize()
-        e2e_steps = max(1, min(args.steps, 3))
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            lat.set_gauge(U_h.numpy())
-            lat.set_clover(w["m0"], w["c_sw"])
-            re = lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
-        torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / e2e_steps
-        line["e2e"] = {"value": V * nrhs / te, "unit": "site·rhs/s", "h2d_bytes_per_step": U.nbytes + b.nbytes,
-                       "d2h_bytes_per_step": b.nbytes, "relres_max": re.relres_max,
-                       "api": "lqcd_set_gauge + lqcd_set_clover + lqcd_solve with pinned host pointers"}
+        extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line)
+        extras_gmres(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, inner, results, line)
+        extras_e2e(args, w, lat, lq, torch, U, b, nrhs, solve_kw, line)
+        extras_oracle_check(args, w, lq, torch, U, b, x_d, lat, nrhs, solve_kw, line)
+    lat.close()
+    del U_d, b_d, x_d
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.skip_extras:
+        if not args.skip_large:
+            extras_gmres_large(args, lq, torch, line)
         # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
         if world == 1 and not args.skip_cpu:
-            its_gpu = statistics.mean(statistics.mean(results[-1].iters_per_rhs) for _ in range(1))
-            k = args.ref_sample_iters
-            ts, tc = oracle_sample(w, k)
-            t_proj = ts + tc * its_gpu / k
-            line["cpu_baseline"] = {"value": V / t_proj, "unit": "site·rhs/s", "cores": cpu_threads(),
-                                    "kind": "oracle",
-                                    "sample": f"numpy FP64 oracle odd-even GMRES on 1 rhs of the same workload: "
-                                              f"set-up {ts:.1f} s + {k} Arnoldi steps {tc:.1f} s, projected to "
-                                              f"{its_gpu:.0f} iterations (the GPU solve's mean per rhs)"}
-    lat.close()
+            extras_cpu_baseline(args, w, line, results)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line):
+    """Operator sweep (dslash GB/s vs the HBM roofline): every nrhs x {c64, c128} x {Schur, full},
+    each point the median of --dslash-reps applies with the L2 flushed in between."""
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    lat.set_gauge(U_d)
+    lat.set_clover(w["m0"], w["c_sw"])
+    sweep = []
+    nr_list = [int(v) for v in args.sweep.split(",")] if args.sweep else [1, 2, 4, 8, 16, 32, 64]
+    for nr in nr_list:
+        for dt in (lq.C64, lq.C128):
+            lat.tune(dt, nr, reps=3)
+            for op in (lq.OP_SCHUR, lq.OP_FULL):
+                tt, nb, units = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
+                sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
+                              "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
+                              "variant": lat.kernel_variant(dt, nr, op),
+                              "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
+                              "site_rhs_per_s": units / tt})
+    del flush
+    line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48b+144)s/site, "
+                      "schur (120b+432)s/odd site", "l2_flush": "512 MB memset between applies",
+                      "applies_per_point": args.dslash_reps, "statistic": "median", "points": sweep}
+
+
+def extras_gmres(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, inner, results, line):
+    """FP64 plain GPU solve vs the mixed solve of the timed steps (same problem)."""
+    lat.set_clover(w["m0"], w["c_sw"])
+    torch.cuda.synchronize()
+    x_d.zero_()
+    t0 = time.perf_counter()
+    r64 = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=lq.C128, restart_len=w["restart"], tol=w["tol"],
+                    max_restarts=args.max_restarts, use_graph=True)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    x64 = x_d.clone()
+    mixed_s = statistics.mean(r.seconds for r in results)
+    x_d.zero_()
+    rg = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, profile=False))
+    torch.cuda.synchronize()
+    diff = [float(torch.linalg.vector_norm(x_d[k] - x64[k]) / torch.linalg.vector_norm(x64[k]))
+            for k in range(nrhs)]
+    other = {}
+    for name, prec in (("c64", lq.C64), ("bf16", lq.BF16S)):
+        if prec == inner:
+            continue
+        x_d.zero_()
+        ro = lat.solve(b_d, x_d, nrhs, **dict(solve_kw, precision=prec, profile=False))
+        torch.cuda.synchronize()
+        other[name] = {"seconds": ro.seconds, "iterations": ro.iterations, "restarts": ro.restarts,
+                       "fp64_residuals": ro.outer_steps, "relres": ro.relres_max}
+    del x64
+    line["gmres"] = {"fp64_s": t64, "mixed_s": mixed_s, "speedup": t64 / mixed_s,
+                     "fp64_iterations": r64.iterations, "mixed_iterations": results[-1].iterations,
+                     "fp64_relres": r64.relres_max, "mixed_relres": results[-1].relres_max,
+                     "mixed_graph_s": rg.seconds, "mixed_vs_fp64_solution_max": max(diff),
+                     "other_inner_storage": other,
+                     "note": "host wall time of one synchronised solve; mixed_s from the timed steps (profiled, "
+                             "no graph replay; mixed_graph_s is the same solve replayed as CUDA graphs)"}
+
+
+def extras_e2e(args, w, lat, lq, torch, U, b, nrhs, solve_kw, line):
+    """End to end through the C ABI with pinned host buffers (copies inside the timed region)."""
+    U_h = torch.from_numpy(U).pin_memory()
+    b_h = torch.from_numpy(b).pin_memory()
+    x_h = torch.zeros_like(b_h).pin_memory()
+    lat.set_gauge(U_h.numpy())
+    lat.set_clover(w["m0"], w["c_sw"])
+    lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_gauge(U_h.numpy())
+        lat.set_clover(w["m0"], w["c_sw"])
+        re = lat.solve(b_h.numpy(), x_h.numpy(), nrhs, **dict(solve_kw, profile=False))
+    torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / e2e_steps
+    line["e2e"] = {"value": V_of(w) * nrhs / te, "unit": "site·rhs/s", "h2d_bytes_per_step": U.nbytes + b.nbytes,
+                   "d2h_bytes_per_step": b.nbytes, "relres_max": re.relres_max,
+                   "api": "lqcd_set_gauge + lqcd_set_clover + lqcd_solve with pinned host pointers"}
+
+
+def V_of(w):
+    d = w["dims"]
+    return d[0] * d[1] * d[2] * d[3]
+
+
+def extras_oracle_check(args, w, lq, torch, U, b, x_d, lat, nrhs, solve_kw, line):
+    """Per-solve checks against the FP64 oracle: (a) the oracle's residual ||b - D x|| / ||b|| of the
+    mixed-precision GPU solution of the timed workload for its first and last rhs; (b) on the 4^4 Haar
+    Wilson lattice (m0 = 0.1, GMRES(30)), the error ||x_gpu - x_oracle|| / ||x_oracle|| of the GPU's
+    FP64 and mixed solves, full and odd-even, against the oracle's own FP64 GMRES solution."""
+    if args.skip_cpu:
+        return
+    import oracle
+    import synthetic as syn
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(w["m0"], w["c_sw"])
+    x_d.zero_()
+    lat.solve(torch.from_numpy(b).cuda(), x_d, nrhs, **dict(solve_kw, profile=False))
+    x = x_d.cpu().numpy()
+    sample = [0, nrhs - 1]
+    A, _ = oracle.diag_blocks(U, w["m0"], w["c_sw"])
+    C = (4.0 + w["m0"]) * np.eye(12) - A
+    r = b[sample] - oracle.apply_D(U, x[sample], w["m0"], C)
+    rel = [float(np.linalg.norm(r[i]) / np.linalg.norm(b[k])) for i, k in enumerate(sample)]
+    small = []
+    dims0 = (4, 4, 4, 4)
+    U0 = syn.gauge_field(dims0, "haar", seed=0)
+    b0 = syn.gaussian_spinors(dims0, 2, 1)
+    lat0 = lq.Lattice(dims0, time_bc=-1)
+    lat0.set_gauge(U0)
+    lat0.set_clover(0.1, 0.0)
+    for op, name in ((lq.OP_FULL, "full"), (lq.OP_SCHUR, "eo")):
+        if op == lq.OP_FULL:
+            xo, _ = oracle.solve_full(U0, None, 0.1, b0, tol=1e-13, m=30, max_restarts=100)
+        else:
+            A0, Ai0 = oracle.diag_blocks(U0, 0.1, 0.0)
+            xo, _ = oracle.solve_eo(U0, A0, Ai0, b0, tol=1e-13, m=30, max_restarts=100)
+        for prec, pname in ((lq.C128, "fp64"), (lq.C64, "mixed")):
+            xg = np.zeros_like(b0)
+            res = lat0.solve(b0, xg, 2, op=op, precision=prec, restart_len=30, tol=1e-10, use_graph=False)
+            err = max(float(np.linalg.norm(xg[k] - xo[k]) / np.linalg.norm(xo[k])) for k in range(2))
+            small.append({"op": name, "precision": pname, "iterations": res.iterations,
+                          "relres_max": res.relres_max, "error_vs_oracle_max": err})
+    lat0.close()
+    line["oracle_check"] = {
+        "timed_workload": {"rhs": sample, "oracle_relres": rel,
+                           "note": "the oracle's FP64 operator applied to the GPU's mixed-precision solution"},
+        "solution_error_4x4x4x4": {"config": "4^4 Haar Wilson m0 0.1, 2 rhs, GMRES(30) to 1e-10; oracle "
+                                             "solution to 1e-13", "solves": small}}
+
+
+def extras_gmres_large(args, lq, torch, line):
+    """The 32^3 x 64 Wilson-clover workload (eps 0.25, 12 rhs, odd-even GMRES(32) to 1e-10):
+    the prescribed mass m0 = -0.3 with the iteration cap --large-cap (status, iterations, true
+    residual), then the companion mass --large-m0 where the solve converges: FP32-inner mixed and
+    FP64 plain GPU time to solution and their ratio."""
+    import synthetic as syn
+    wl = WORKLOADS["solve-large"]
+    dims, nrhs = wl["dims"], wl["nrhs"]
+    t0 = time.perf_counter()
+    U = syn.gauge_field(dims, "exp", wl["eps"], seed=wl["gauge_seed"])
+    b = syn.gaussian_spinors(dims, nrhs, wl["rhs_seed"])
+    t_gen = time.perf_counter() - t0
+    U_d = torch.from_numpy(U).cuda()
+    b_d = torch.from_numpy(b).cuda()
+    del U, b
+    x_d = torch.zeros_like(b_d)
+    lat = lq.Lattice(dims, time_bc=-1)
+    lat.set_gauge(U_d)
+    out = {"lattice": "x".join(str(d) for d in dims[::-1]), "nrhs": nrhs, "gauge": f"exp(i*{wl['eps']}*H)",
+           "c_sw": wl["c_sw"], "solver": "odd-even GMRES(32), tol 1e-10 (true residual, per rhs)",
+           "input_generation_s": t_gen}
+
+    def one(m0, precision, cap):
+        lat.set_clover(m0, wl["c_sw"])
+        x_d.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=precision, restart_len=wl["restart"],
+                      tol=wl["tol"], max_restarts=cap, use_graph=True)
+        torch.cuda.synchronize()
+        return {"m0": m0, "precision": "fp32 inner / fp64 refinement" if precision == lq.C64 else "fp64",
+                "status": {lq.OK: "converged", lq.NOT_CONVERGED: "not converged"}.get(r.status, str(r.status)),
+                "seconds": time.perf_counter() - t, "iterations": r.iterations, "cycles": r.restarts,
+                "fp64_residuals": r.outer_steps, "relres_max": r.relres_max}
+
+    lat.set_clover(wl["m0"], wl["c_sw"])
+    lat.tune(lq.C64, nrhs, reps=2)
+    lat.tune(lq.C128, nrhs, reps=1)
+    out["prescribed"] = one(wl["m0"], lq.C64, args.large_cap)
+    out["prescribed"]["note"] = f"capped at {args.large_cap} Arnoldi cycles"
+    mixed = one(args.large_m0, lq.C64, args.max_restarts)
+    fp64 = one(args.large_m0, lq.C128, args.max_restarts)
+    out["companion"] = {"m0": args.large_m0, "mixed": mixed, "fp64": fp64,
+                        "speedup_mixed_vs_fp64": fp64["seconds"] / mixed["seconds"]}
+    lat.close()
+    del U_d, b_d, x_d
+    torch.cuda.empty_cache()
+    line["gmres_large"] = out
+
+
+def extras_cpu_baseline(args, w, line, results):
+    """The oracle as it stands on the host cores: the FP64 Schur and full operator applied once each to
+    --cpu-nrhs rhs of the timed workload's lattice (measured, no projection); the projection of the
+    oracle's odd-even solve to the GPU solve's iteration count is reported beside it as an extra."""
+    smp = oracle_apply_sample(w, args.cpu_nrhs)
+    its_gpu = statistics.mean(results[-1].iters_per_rhs)
+    U, A, Ainv, b1, t_setup = oracle_setup(w)
+    m = args.ref_cycle_steps
+    t_cyc = oracle_cycle(U, A, Ainv, b1, m)
+    t_iter, t_fixed = oracle_cost_model(U, A, Ainv, b1, m, t_cyc)
+    t_proj = t_setup + its_gpu * t_iter + -(-its_gpu // 32) * t_fixed
+    line["cpu_baseline"] = {
+        "value": smp["schur"], "unit": "site·rhs/s (FP64 odd-even Schur apply)", "cores": cpu_threads(),
+        "kind": "oracle",
+        "sample": f"numpy FP64 oracle on the {w['name'].split(' ')[1]} lattice: one Schur apply and one full "
+                  f"apply on {smp['nrhs']} Gaussian rhs, timed ({smp['schur_s']:.1f} s / {smp['full_s']:.1f} s; "
+                  f"clover set-up {smp['setup_s']:.1f} s not included)",
+        "full_apply_site_rhs_per_s": smp["full"],
+        "solve_projection": {"value": V_of(w) / t_proj, "unit": "site·rhs/s (solve, projected)",
+                             "method": f"oracle GMRES cycles on 1 rhs: {t_iter:.2f} s per Arnoldi step, {t_fixed:.2f} s "
+                                       f"fixed per cycle, scaled to {its_gpu:.0f} iterations + set-up {t_setup:.1f} s"}}
 
 
 def main():
@@ -719,11 +904,19 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="solve", choices=sorted(WORKLOADS))
     ap.add_argument("--sweep", default="", help="comma-separated nrhs list for the operator sweep")
-    ap.add_argument("--dslash-reps", type=int, default=20)
+    ap.add_argument("--dslash-reps", type=int, default=50)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--ref-sample-iters", type=int, default=4)
-    ap.add_argument("--ref-iterations", type=int, default=535)
+    ap.add_argument("--ref-cycle-steps", type=int, default=2,
+                    help="oracle arm: Arnoldi steps of the oracle GMRES cycle timed per step")
+    ap.add_argument("--ref-iterations", type=int, default=535,
+                    help="oracle arm: iterations per rhs of the GPU solve the oracle's cost is projected to")
+    ap.add_argument("--cpu-nrhs", type=int, default=4, help="rhs of the timed oracle operator applies")
+    ap.add_argument("--skip-large", action="store_true", help="skip the 32^3 x 64 GMRES comparison")
+    ap.add_argument("--large-cap", type=int, default=64,
+                    help="Arnoldi cycles allowed for the prescribed-mass 32^3 x 64 solve")
+    ap.add_argument("--large-m0", type=float, default=-0.1,
+                    help="companion mass of the 32^3 x 64 solve (mixed vs FP64 time to solution)")
     ap.add_argument("--m0", type=float, default=None,
                     help="companion run: replace the workload's bare mass (reported as such in config)")
     ap.add_argument("--max-restarts", type=int, default=500)

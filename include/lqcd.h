@@ -306,10 +306,14 @@ lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_pa
  * allocating routine. Requires V/2 * 12 * nrhs * sizeof(complex) <= that size;
  * larger requests return LQCD_ERR_ARG with a message and do nothing.
  * The first call on each device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture. All calls share the one array and it keeps the last call's contents
- * (every call overwrites all it reads): calls that overlap on the GPU, e.g. on
- * two streams at once, race and give wrong results. Requires set_gauge and
+ * device current) and caches it for the rest of the process; make that first
+ * call before any stream capture. The cached address stays valid as long as the
+ * device's primary context does: after a cudaDeviceReset in the same process the
+ * library (every context and this cache) must not be used again. The device that
+ * was current at lqcd_set_gauge must be current here (LQCD_ERR_STATE otherwise).
+ * All calls share the one array and it keeps the last call's contents (every
+ * call overwrites all it reads): calls that overlap on the GPU, e.g. on two
+ * streams at once, race and give wrong results. Requires set_gauge and
  * set_clover (which allocate, at set-up). */
 lqcd_status lqcd_apply_schur_noalloc(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
                                      const void* in, void* out, void* stream);

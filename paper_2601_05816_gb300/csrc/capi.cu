@@ -117,6 +117,12 @@ static DslashArgs<Real> base_args(lqcd_ctx ctx, int nrhs, bool f64) {
   a.blocks = (const Real*)(f64 ? ctx->blk64 : ctx->blk32);
   a.blocks_inv = (const Real*)(f64 ? ctx->inv64 : ctx->inv32);
   a.num_sms = ctx->num_sms;
+  if (!f64) {
+    a.links_aos = ctx->links32_aos;
+    a.blocks_aos = ctx->blk32_aos;
+    a.blocks_inv_aos = ctx->inv32_aos;
+  }
+  a.err = ctx->ws.count("wait_flag") ? (int*)ctx->ws["wait_flag"].p : nullptr;
   return a;
 }
 
@@ -351,6 +357,7 @@ lqcd_status lqcd_free(lqcd_ctx ctx) {
   for (auto& e : ctx->prof_events) cudaEventDestroy(e);
   free_ptr(ctx->links64); free_ptr(ctx->links32);
   free_ptr(ctx->blk64); free_ptr(ctx->inv64); free_ptr(ctx->blk32); free_ptr(ctx->inv32);
+  free_ptr(ctx->links32_aos); free_ptr(ctx->blk32_aos); free_ptr(ctx->inv32_aos);
   void* e = ctx->d_err; free_ptr(e);
   for (auto& kv : ctx->ws) free_ptr(kv.second.p);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -370,6 +377,8 @@ lqcd_status lqcd_set_gauge(lqcd_ctx ctx, const void* U, void* stream) {
     LQCD_CUDA(cudaMalloc(&ctx->links64, 36 * V * sizeof(double2)), "cudaMalloc(links64)");
     LQCD_CUDA(cudaMalloc(&ctx->links32, 36 * V * sizeof(float2)), "cudaMalloc(links32)");
     LQCD_CUDA(cudaMalloc((void**)&ctx->d_err, sizeof(int)), "cudaMalloc(err)");
+    LQCD_CUDA(cudaMalloc(&ctx->links32_aos, 40 * V * sizeof(float2)), "cudaMalloc(links32 site-major)");
+    if (wait_flag(ctx) == nullptr) return set_error(LQCD_ERR_OOM, "lqcd_set_gauge: cannot allocate the wait flag");
   }
   const void* src = U;
   if (!is_device_pointer(U)) {
@@ -381,6 +390,7 @@ lqcd_status lqcd_set_gauge(lqcd_ctx ctx, const void* U, void* stream) {
     src = tmp;
   }
   LQCD_CUDA(launch_gauge_pack(ctx->g, ctx->time_bc, src, ctx->links64, ctx->links32, s), "gauge pack");
+  LQCD_CUDA(launch_links_aos(ctx->g.V, ctx->links32, ctx->links32_aos, s), "links site-major");
   if (src != U) LQCD_CUDA(cudaStreamSynchronize(s), "gauge upload sync");
   ctx->have_gauge = true;
   ctx->have_blocks = false;
@@ -399,6 +409,8 @@ lqcd_status lqcd_set_clover(lqcd_ctx ctx, double m0, double c_sw, void* stream) 
     LQCD_CUDA(cudaMalloc(&ctx->inv64, 72 * V * sizeof(double)), "cudaMalloc(inv64)");
     LQCD_CUDA(cudaMalloc(&ctx->blk32, 72 * V * sizeof(float)), "cudaMalloc(blocks32)");
     LQCD_CUDA(cudaMalloc(&ctx->inv32, 72 * V * sizeof(float)), "cudaMalloc(inv32)");
+    LQCD_CUDA(cudaMalloc(&ctx->blk32_aos, 72 * V * sizeof(float)), "cudaMalloc(blocks32 site-major)");
+    LQCD_CUDA(cudaMalloc(&ctx->inv32_aos, 72 * V * sizeof(float)), "cudaMalloc(inv32 site-major)");
   }
   void* leaf;
   lqcd_status st = workspace(ctx, "clover_leaves", 54 * V * sizeof(double2), &leaf);
@@ -407,6 +419,8 @@ lqcd_status lqcd_set_clover(lqcd_ctx ctx, double m0, double c_sw, void* stream) 
   LQCD_CUDA(launch_clover_build(ctx->g, ctx->links64, m0, c_sw, leaf, ctx->blk64, ctx->inv64, ctx->blk32,
                                 ctx->inv32, ctx->d_err, s),
             "clover build");
+  LQCD_CUDA(launch_blocks_aos(ctx->g.V, ctx->blk32, ctx->blk32_aos, s), "blocks site-major");
+  LQCD_CUDA(launch_blocks_aos(ctx->g.V, ctx->inv32, ctx->inv32_aos, s), "inverse blocks site-major");
   int herr = 0;
   LQCD_CUDA(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read err");
   LQCD_CUDA(cudaStreamSynchronize(s), "clover sync");

@@ -40,6 +40,9 @@ struct lqcd_ctx_s {
   void* inv64 = nullptr;    // A^{-1}
   void* blk32 = nullptr;    // A, 72 floats per site (SoA float4 chunks)
   void* inv32 = nullptr;
+  void* links32_aos = nullptr;  // [4][V][10] float2, links padded to 80 bytes (ring kernel)
+  void* blk32_aos = nullptr;    // [V][72] float, A per site (ring kernel)
+  void* inv32_aos = nullptr;    // [V][72] float, A^{-1} per site (ring kernel)
   int* d_err = nullptr;     // device status bitmask
   std::map<std::string, lqcd::Buffer> ws;
   cudaStream_t capture_stream = nullptr;

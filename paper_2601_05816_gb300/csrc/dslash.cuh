@@ -56,6 +56,12 @@ struct DslashArgs {
   const int* skip;     // optional: return at once when *skip != 0
   int loop_chunk;      // persistent variants: target sites per CTA (set by the launcher)
   int num_sms;         // SMs of the context's device (persistent variants size their grid by it)
+  // FP32 copies for the bulk-copy ring kernel (dslash_ring.cuh), null where not built:
+  const void* links_aos;       // [4][V][10] float2: each link's 9 entries padded to 80 bytes, eo site order
+  const void* blocks_aos;      // [V][72] float: A(x) per site (the 16-byte chunks of `blocks` in site-major order)
+  const void* blocks_inv_aos;  // [V][72] float: A(x)^{-1}
+  int* err;                    // set (bit 0) when a bounded pipeline wait gives up
+  int ring_slots;              // ring kernel: slots per warp (set by its launcher)
 };
 
 // NR complex numbers (NR consecutive rhs of one component).
@@ -483,6 +489,8 @@ struct DslashVariant {
   int loop;    // direct loads: 1 = persistent CTAs walking contiguous chunks of sites
   int nrhs_fixed = 0;  // > 0: compiled for this rhs count only (immediate component offsets)
   int prefetch = 0;    // with nrhs_fixed: L1 prefetch of the operands this many directions ahead
+  int ring_warps = 0;  // > 0: the bulk-copy ring kernel (dslash_ring.cuh) with this many warps per CTA
+  int ring_slots = 0;  //       and this many ring slots per warp
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);

@@ -1,16 +1,24 @@
 // Variant tables and dispatch of the multi-rhs hopping kernel.
 #include "dslash_async.cuh"
+#include "dslash_ring.cuh"
 
 namespace lqcd {
 
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
-//  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance}
+//  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance,
+//  ring kernel warps per CTA, ring slots per warp}
 const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
                              {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16},
                              {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
                              {2, 128, 4, 0, 0, 0, 32}, {2, 128, 4, 0, 0, 0, 32, 1},
-                             {2, 128, 4, 0, 0, 0, 64}, {2, 128, 4, 0, 0, 0, 64, 1}};
+                             {2, 128, 4, 0, 0, 0, 64}, {2, 128, 4, 0, 0, 0, 64, 1},
+                             // bulk-copy ring kernel (dslash_ring.cuh): warps per CTA, ring slots per warp
+                             {2, 256, 1, 0, 0, 0, 16, 0, 8, 3}, {2, 256, 1, 0, 0, 0, 16, 0, 8, 2},
+                             {2, 192, 1, 0, 0, 0, 16, 0, 6, 4}, {2, 128, 1, 0, 0, 0, 16, 0, 4, 3},
+                             {2, 256, 1, 0, 0, 0, 32, 0, 8, 3}, {2, 192, 1, 0, 0, 0, 32, 0, 6, 4},
+                             {2, 256, 1, 0, 0, 0, 64, 0, 8, 3}, {2, 256, 1, 0, 0, 0, 64, 0, 8, 4},
+                             {2, 192, 1, 0, 0, 0, 64, 0, 6, 4}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -40,6 +48,9 @@ LQCD_EXTERN_NRHS(128, 4, 32, 1)
 LQCD_EXTERN_NRHS(128, 4, 64, 0)
 LQCD_EXTERN_NRHS(128, 4, 64, 1)
 #undef LQCD_EXTERN_NRHS
+extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
@@ -69,6 +80,13 @@ template <>
 cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int post_mode, int variant,
                                  cudaStream_t s) {
   if (!dslash_variant_ok(false, variant, a.lay.nrhs)) variant = dslash_default_variant(false, a.lay.nrhs);
+  const DslashVariant v = kF32[variant];
+  if (v.ring_warps > 0) {
+    if (v.nrhs_fixed == 16) return launch_dslash_ring<16>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
+    if (v.nrhs_fixed == 32) return launch_dslash_ring<32>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
+    if (v.nrhs_fixed == 64) return launch_dslash_ring<64>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
+    return cudaErrorInvalidValue;
+  }
   switch (variant) {
     case 0: return launch_dslash_variant<float, 2, 128, 1, false, false>(a, self_mode, post_mode, s);
     case 1: return launch_dslash_variant<float, 2, 128, 4, false, false>(a, self_mode, post_mode, s);

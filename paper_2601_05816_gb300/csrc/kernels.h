@@ -12,6 +12,9 @@ namespace lqcd {
 // bf16: packed side BF16 pairs, canonical side complex64 (f64 ignored).
 cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, bool to_packed,
                                  bool f64, const void* in, void* out, cudaStream_t stream, bool bf16 = false);
+// Site-major FP32 copies for the ring hopping kernel: links [4][V][10] float2, blocks [V][72] float.
+cudaError_t launch_links_aos(int V, const void* links32, void* aos, cudaStream_t s);
+cudaError_t launch_blocks_aos(int V, const void* blk32, void* aos, cudaStream_t s);
 cudaError_t launch_gauge_pack(const Geom& g, int time_bc, const void* U, void* l64, void* l32,
                               cudaStream_t stream);
 

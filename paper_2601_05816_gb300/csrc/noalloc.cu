@@ -28,11 +28,18 @@ void* g_scratch_address[kMaxDevices] = {nullptr};
 
 // Device address of g_noalloc_scratch on the current device, looked up once per
 // device with that device current. In host code the symbol itself is only a
-// host-side stand-in and must never be passed to a kernel.
-lqcd_status scratch_address(void** out) {
+// host-side stand-in and must never be passed to a kernel. The current device
+// must be the one holding the context's fields (the device that was current at
+// lqcd_set_gauge): the kernels read the links there and write the scratch array
+// of the current device.
+lqcd_status scratch_address(int ctx_device, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return lqcd::cuda_error(e, "lqcd_apply_schur_noalloc: cudaGetDevice");
+  if (dev != ctx_device)
+    return lqcd::set_error(LQCD_ERR_STATE,
+                           "lqcd_apply_schur_noalloc: device %d is current but the context's fields live on "
+                           "device %d; make that device current first", dev, ctx_device);
   if (dev < 0 || dev >= kMaxDevices)
     return lqcd::set_error(LQCD_ERR_ARG, "lqcd_apply_schur_noalloc: device ordinal %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
@@ -70,7 +77,7 @@ lqcd_status lqcd_apply_schur_noalloc(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, c
                            "complex), more than the fixed %zu-byte scratch; use lqcd_apply_packed instead",
                            need, kNoallocScratchBytes);
   void* scratch = nullptr;
-  lqcd_status st = scratch_address(&scratch);
+  lqcd_status st = scratch_address(ctx->device, &scratch);
   if (st != LQCD_OK) return st;
   // Pass A overwrites every element of the scratch block before pass B reads it,
   // so nothing left over from an earlier call is ever used.

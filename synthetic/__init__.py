@@ -80,30 +80,50 @@ def _reunitarise_cm(m: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2])
 
 
+def _exp_chunk(h: np.ndarray, eps: float, lam: np.ndarray) -> np.ndarray:
+    """exp(i eps H) for one chunk of Gell-Mann coefficient rows h [m, 8]; returns [m, 3, 3]."""
+    # X = i eps H, component-major [3, 3, m]
+    H = np.einsum("na,aij->ijn", h, lam) * 0.5
+    X = 1j * eps * H
+    norm = float(np.sqrt(np.max(np.sum(np.abs(X) ** 2, axis=(0, 1))))) if X.shape[2] else 0.0
+    sq = max(0, int(np.ceil(np.log2(max(norm, 1e-300) / 0.25))))
+    Xs = X / (2.0 ** sq)
+    eye = np.zeros_like(Xs)
+    for i in range(3):
+        eye[i, i] = 1.0
+    # Horner form of the degree-12 Taylor polynomial: |Xs| <= 1/4 gives < 1e-17.
+    E = eye.copy()
+    for k in range(12, 0, -1):
+        E = eye + _cm_matmul(Xs, E) / k
+    for _ in range(sq):
+        E = _cm_matmul(E, E)
+    E = _reunitarise_cm(E)
+    return np.transpose(E, (2, 0, 1))
+
+
 def exp_su3(g: np.random.Generator, n: int, eps: float, chunk: int = 1 << 20) -> np.ndarray:
-    """n links U = exp(i eps H), H Gaussian traceless Hermitian; returns [n, 3, 3]."""
+    """n links U = exp(i eps H), H Gaussian traceless Hermitian; returns [n, 3, 3].
+
+    The random numbers are drawn in one call; the chunks of 2^20 links are then
+    exponentiated independently (on a few threads for large fields: numpy releases
+    the interpreter lock inside its array operations), so the result does not
+    depend on the thread count."""
     lam = _gell_mann()
     out = np.empty((n, 3, 3), dtype=np.complex128)
     h_all = g.standard_normal((n, 8))
-    for s in range(0, n, chunk):
-        h = h_all[s:s + chunk]
-        # X = i eps H, component-major [3, 3, m]
-        H = np.einsum("na,aij->ijn", h, lam) * 0.5
-        X = 1j * eps * H
-        norm = float(np.sqrt(np.max(np.sum(np.abs(X) ** 2, axis=(0, 1))))) if X.shape[2] else 0.0
-        sq = max(0, int(np.ceil(np.log2(max(norm, 1e-300) / 0.25))))
-        Xs = X / (2.0 ** sq)
-        eye = np.zeros_like(Xs)
-        for i in range(3):
-            eye[i, i] = 1.0
-        # Horner form of the degree-12 Taylor polynomial: |Xs| <= 1/4 gives < 1e-17.
-        E = eye.copy()
-        for k in range(12, 0, -1):
-            E = eye + _cm_matmul(Xs, E) / k
-        for _ in range(sq):
-            E = _cm_matmul(E, E)
-        E = _reunitarise_cm(E)
-        out[s:s + chunk] = np.transpose(E, (2, 0, 1))
+    starts = list(range(0, n, chunk))
+
+    def work(s):
+        out[s:s + chunk] = _exp_chunk(h_all[s:s + chunk], eps, lam)
+
+    if len(starts) > 2:
+        import concurrent.futures as cf
+        import os
+        with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1, 16)) as ex:
+            list(ex.map(work, starts))
+    else:
+        for s in starts:
+            work(s)
     return out
 
 

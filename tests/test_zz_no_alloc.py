@@ -5,16 +5,20 @@ allocate device memory during their run (their own allocator owns the memory,
 or their footprint must be fixed in advance, or their loop cannot take the
 synchronisation of a cudaMalloc). It keeps its intermediate block in a fixed
 device array instead of workspace. This test calls it through the C ABI twice
-in a row and compares each output with lqcd_apply_packed(LQCD_OP_SCHUR) within
-the operator tolerances of the other GPU tests (FP64 1e-12, FP32 5e-6), and
-checks that a request larger than the fixed array is refused on the host. The
-file name makes pytest collect it last.
+in a row and compares each output with lqcd_apply_packed(LQCD_OP_SCHUR) and with
+the FP64 oracle's Schur operator within the operator tolerances of the other GPU
+tests (FP64 1e-12, FP32 5e-6); checks on a fresh lattice context, before any
+other apply on it, that the call leaves the device's free memory unchanged (no
+workspace allocated); and checks that a request larger than the fixed array or a
+call with another device current is refused on the host. The file name makes
+pytest collect it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +51,7 @@ def test_noalloc_schur_matches_regular_apply_twice(lib, dtype, tol):
     lat = lq.Lattice(dims)
     lat.set_gauge(torch.from_numpy(U).cuda())
     lat.set_clover(-0.2, 1.0)
+    A, Ainv = oracle.diag_blocks(U, -0.2, 1.0)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         psi = syn.gaussian_spinors((8, 8, 8, 4), nrhs, 40 + call).reshape(nrhs, lat.V // 2, 4, 3)
@@ -65,7 +70,56 @@ def test_noalloc_schur_matches_regular_apply_twice(lib, dtype, tol):
         r = ref.cpu().numpy().astype(np.complex128).reshape(-1, nrhs)
         err = max(np.linalg.norm(g[:, k] - r[:, k]) / np.linalg.norm(r[:, k]) for k in range(nrhs))
         assert err <= tol, (call, err)
+        # and the oracle's S psi_o on the same (rounded) input
+        ref_o = oracle.apply_schur(U, A, Ainv, t.cpu().numpy().astype(np.complex128))
+        out = torch.empty_like(t)
+        lat.unpack(lq.SITES_ODD, nrhs, got, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy().astype(np.complex128).reshape(nrhs, -1)
+        ro = ref_o.reshape(nrhs, -1)
+        err_o = max(np.linalg.norm(o[k] - ro[k]) / np.linalg.norm(ro[k]) for k in range(nrhs))
+        assert err_o <= tol, (call, err_o)
     lat.close()
+
+
+def test_noalloc_allocates_nothing_on_a_fresh_context(lib):
+    """A fresh lattice context that has never applied an operator: the no-alloc Schur apply leaves
+    the device's free memory unchanged (the regular apply would allocate its workspace here). One
+    earlier call on another context loads the library's scratch array first (CUDA loads a module's
+    device globals when the module is first used)."""
+    dims = (16, 8, 8, 8)
+    nrhs = 8    # the regular apply's intermediate block: V/2 * 12 * 8 * 8 bytes = 3.1 MB
+    U = syn.gauge_field(dims, "exp", 0.3, seed=32)
+    stream = torch.cuda.current_stream().cuda_stream
+    warm = lq.Lattice(dims)
+    warm.set_gauge(torch.from_numpy(U).cuda())
+    warm.set_clover(-0.2, 1.0)
+    a = warm.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
+    a.zero_()
+    b = torch.empty_like(a)
+    assert lib.lqcd_apply_schur_noalloc(warm.handle, lq.C64, nrhs, a.data_ptr(), b.data_ptr(), stream) == lq.OK
+    torch.cuda.synchronize()
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(-0.2, 1.0)
+    pin = lat.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
+    pin.normal_()
+    pout = torch.empty_like(pin)
+    ref = torch.empty_like(pin)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        st = lib.lqcd_apply_schur_noalloc(lat.handle, lq.C64, nrhs, pin.data_ptr(), pout.data_ptr(), stream)
+        assert st == lq.OK, lib.lqcd_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    # the regular apply on the same fresh context does allocate its workspace (the check has teeth)
+    lat.apply_packed(lq.OP_SCHUR, nrhs, pin, ref)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free0
+    assert torch.allclose(ref, pout, rtol=0, atol=1e-5 * float(ref.abs().max()))
+    lat.close()
+    warm.close()
 
 
 def test_noalloc_rejects_oversized_request(lib):
