@@ -337,7 +337,8 @@ def run_kernel_workload(args, w):
     g = torch.Generator(device="cuda").manual_seed(7 + rank)
     tuning = None
     if w["kind"] == "apply":
-        tuning = lat.tune(lq.C64, nrhs, reps=5)
+        if not (args.no_tune and args.variant >= 0):
+            tuning = lat.tune(lq.C64, nrhs, reps=5)
         if args.variant >= 0:
             lat.set_kernel_variant(lq.C64, nrhs, lq.OP_SCHUR, args.variant)
         pin = lat.packed_empty(lq.C64, lq.SITES_ODD, nrhs)
@@ -930,6 +931,8 @@ def main():
                     help="solve workloads: Gram-Schmidt of the Arnoldi step (0 CGS1, 1 CGS2, 2 delayed CGS2)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="apply workload with --variant: skip the autotuner (only that variant launches)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.m0 is not None:

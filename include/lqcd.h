@@ -227,6 +227,12 @@ typedef struct {
                          gamma5 D^{-1} gamma5 b (D^dagger = gamma5 D gamma5, Sec. III-A-1's
                          operator is gamma5-Hermitian); tol and the reported residuals
                          refer to D^dagger */
+  int compact;        /* 1: when at an FP64 restart at least max(1, n/8) of the n rhs still
+                         in the block have met tol, repack the others into a block of fewer
+                         rhs (library workspace) and continue on it, so retired rhs no longer
+                         pass through the operator and Gram-Schmidt kernels; the FP64 residual
+                         of the new block is recomputed once. 0: retired rhs stay in the block
+                         and only stop contributing basis vectors */
 } lqcd_solve_params;
 
 typedef struct {

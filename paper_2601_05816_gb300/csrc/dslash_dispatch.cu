@@ -13,12 +13,14 @@ const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 12
                              {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
                              {2, 128, 4, 0, 0, 0, 32}, {2, 128, 4, 0, 0, 0, 32, 1},
                              {2, 128, 4, 0, 0, 0, 64}, {2, 128, 4, 0, 0, 0, 64, 1},
-                             // bulk-copy ring kernel (dslash_ring.cuh): warps per CTA, ring slots per warp
-                             {2, 256, 1, 0, 0, 0, 16, 0, 8, 3}, {2, 256, 1, 0, 0, 0, 16, 0, 8, 2},
-                             {2, 192, 1, 0, 0, 0, 16, 0, 6, 4}, {2, 128, 1, 0, 0, 0, 16, 0, 4, 3},
-                             {2, 256, 1, 0, 0, 0, 32, 0, 8, 3}, {2, 192, 1, 0, 0, 0, 32, 0, 6, 4},
-                             {2, 256, 1, 0, 0, 0, 64, 0, 8, 3}, {2, 256, 1, 0, 0, 0, 64, 0, 8, 4},
-                             {2, 192, 1, 0, 0, 0, 64, 0, 6, 4}};
+                             // bulk-copy ring kernel (dslash_ring.cuh): CTAs per SM (minb), warps per CTA,
+                             // ring slots per warp
+                             {2, 256, 1, 0, 0, 0, 16, 0, 8, 3}, {2, 384, 1, 0, 0, 0, 16, 0, 12, 2},
+                             {2, 448, 1, 0, 0, 0, 16, 0, 14, 2}, {2, 224, 2, 0, 0, 0, 16, 0, 7, 2},
+                             {2, 192, 2, 0, 0, 0, 16, 0, 6, 2}, {2, 512, 1, 0, 0, 0, 16, 0, 16, 1},
+                             {2, 384, 1, 0, 0, 0, 32, 0, 12, 2}, {2, 224, 2, 0, 0, 0, 32, 0, 7, 2},
+                             {2, 384, 1, 0, 0, 0, 64, 0, 12, 2}, {2, 224, 2, 0, 0, 0, 64, 0, 7, 2},
+                             {2, 256, 1, 0, 0, 0, 64, 0, 8, 3}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -48,9 +50,9 @@ LQCD_EXTERN_NRHS(128, 4, 32, 1)
 LQCD_EXTERN_NRHS(128, 4, 64, 0)
 LQCD_EXTERN_NRHS(128, 4, 64, 1)
 #undef LQCD_EXTERN_NRHS
-extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
-extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 128, 4, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_variant<double, 1, 256, 1, false, false>(const DslashArgs<double>&, int, int, cudaStream_t);
@@ -82,9 +84,10 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
   if (!dslash_variant_ok(false, variant, a.lay.nrhs)) variant = dslash_default_variant(false, a.lay.nrhs);
   const DslashVariant v = kF32[variant];
   if (v.ring_warps > 0) {
-    if (v.nrhs_fixed == 16) return launch_dslash_ring<16>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
-    if (v.nrhs_fixed == 32) return launch_dslash_ring<32>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
-    if (v.nrhs_fixed == 64) return launch_dslash_ring<64>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, s);
+    const int cps = v.minb;  // resident CTAs per SM the variant is built for
+    if (v.nrhs_fixed == 16) return launch_dslash_ring<16>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, cps, s);
+    if (v.nrhs_fixed == 32) return launch_dslash_ring<32>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, cps, s);
+    if (v.nrhs_fixed == 64) return launch_dslash_ring<64>(a, self_mode, post_mode, v.ring_warps, v.ring_slots, cps, s);
     return cudaErrorInvalidValue;
   }
   switch (variant) {

@@ -63,11 +63,19 @@ __device__ __forceinline__ int neighbour_lex_k(const Geom& g, const Coord& c, in
   }
 }
 
-// The operands of one slot (sequence number seq of this warp: target group it, slot s),
-// posted on the slot's barrier. Called by the whole warp.
+// Target site of producer lane l (< TPW) of a target group: parity, checkerboard index,
+// coordinates. Computed once per group (the divisions of site_coords), reused for its slots.
+struct ProdSite {
+  int group;  // first target index of the group these values belong to (-1: none yet)
+  int p, cb;
+  Coord c;
+};
+
+// The operands of slot s (0..7: hopping direction s; 8: site-local operands) of the target
+// group starting at `first`, posted on the slot's barrier. Called by the whole warp.
 template <int SELF, int POST, int NRHS>
 __device__ __forceinline__ void produce(const DslashArgs<float>& a, unsigned char* slot, uint64_t* bar, int first,
-                                        int s, int lane) {
+                                        int s, int lane, ProdSite& ps) {
   using Sh = Shape<NRHS>;
   constexpr bool SELF_IN = SELF != SELF_NONE;
   constexpr bool BLOCK = SELF == SELF_BLOCK || POST == POST_BLOCKINV;
@@ -77,18 +85,21 @@ __device__ __forceinline__ void produce(const DslashArgs<float>& a, unsigned cha
   if (lane == 0) mbar_expect_tx(bar, bytes);
   __syncwarp();
   if (lane < nvalid) {
-    const int site = first + lane;
-    int p, cb;
-    if (a.full) {
-      p = site >= a.g.Vh ? 1 : 0;
-      cb = site - p * a.g.Vh;
-    } else {
-      p = a.target_parity;
-      cb = site;
+    if (ps.group != first) {
+      const int site = first + lane;
+      if (a.full) {
+        ps.p = site >= a.g.Vh ? 1 : 0;
+        ps.cb = site - ps.p * a.g.Vh;
+      } else {
+        ps.p = a.target_parity;
+        ps.cb = site;
+      }
+      ps.c = site_coords(a.g, ps.p, ps.cb);
+      ps.group = first;
     }
+    const int p = ps.p, cb = ps.cb;
     if (s < 8) {
-      const Coord c = site_coords(a.g, p, cb);
-      const int ncb = neighbour_lex_k(a.g, c, s) >> 1;
+      const int ncb = neighbour_lex_k(a.g, ps.c, s) >> 1;
       const float2* hin = a.hop_in + (a.full ? (int64_t)(1 - p) * a.half_elems : 0);
       bulk_load(slot + (size_t)lane * Sh::SP, hin + (int64_t)ncb * 12 * NRHS, Sh::SP, bar);
       const int mu = s >> 1;
@@ -143,8 +154,8 @@ __device__ __forceinline__ bool wait_slot(uint64_t* bars, int K, int seq) {
   return __all_sync(0xffffffffu, mine);
 }
 
-template <int SELF, int POST, int NRHS>
-__global__ void __launch_bounds__(256, 1) dslash_ring_kernel(const DslashArgs<float> a) {
+template <int SELF, int POST, int NRHS, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) dslash_ring_kernel(const DslashArgs<float> a) {
   using Sh = Shape<NRHS>;
   constexpr bool HAS_SITE = SELF != SELF_NONE || POST == POST_BLOCKINV;
   constexpr int NSLOT = 8 + (HAS_SITE ? 1 : 0);
@@ -170,10 +181,12 @@ __global__ void __launch_bounds__(256, 1) dslash_ring_kernel(const DslashArgs<fl
   const int r0 = (lane % Sh::G) * 2;  // and its two rhs
 
   int issued = 0;
+  ProdSite ps;
+  ps.group = -1;
   auto post = [&](int seq) {
     const int it = seq / NSLOT;
     produce<SELF, POST, NRHS>(a, ring + (size_t)(seq % K) * Sh::SLOT, &bars[seq % K],
-                              (task0 + it * tstride) * Sh::TPW, seq - it * NSLOT, lane);
+                              (task0 + it * tstride) * Sh::TPW, seq - it * NSLOT, lane, ps);
   };
   for (; issued < K - 1 && issued < total; ++issued) post(issued);
 
@@ -304,16 +317,17 @@ __global__ void __launch_bounds__(256, 1) dslash_ring_kernel(const DslashArgs<fl
 // and `slots` ring slots per warp: a persistent grid of at most (resident CTAs per SM)
 // x (SMs) CTAs. cudaErrorInvalidValue if the arguments do not fit (rhs count, site
 // tile, missing padded link / block copies, shared memory, unsupported combination).
-template <int SELF, int POST, int NRHS>
+template <int SELF, int POST, int NRHS, int MAXT, int MINB>
 cudaError_t launch_dslash_ring_one(DslashArgs<float> a, int warps, int slots, cudaStream_t stream) {
-  auto kern = ring::dslash_ring_kernel<SELF, POST, NRHS>;
+  if (warps * 32 > MAXT) return cudaErrorInvalidValue;
+  auto kern = ring::dslash_ring_kernel<SELF, POST, NRHS, MAXT, MINB>;
   static std::once_flag attr;
   std::call_once(attr, [&] {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   const size_t smem = ring::smem_bytes<NRHS>(warps, slots);
   // resident CTAs per SM of this launch shape (depends on the kernel and the architecture only)
-  static std::atomic<int> occ_cache[9][9];
+  static std::atomic<int> occ_cache[17][9];
   int occ = occ_cache[warps][slots].load(std::memory_order_relaxed);
   if (occ == 0) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, warps * 32, smem);
@@ -330,27 +344,39 @@ cudaError_t launch_dslash_ring_one(DslashArgs<float> a, int warps, int slots, cu
   return cudaGetLastError();
 }
 
+// Register budgets of the ring kernel: up to 8 warps per CTA with one CTA per SM, or
+// up to 7 warps per CTA with two CTAs per SM (<= 146 registers), or up to 16 warps per
+// CTA with one CTA per SM (<= 128 registers).
+template <int SELF, int POST, int NRHS>
+cudaError_t launch_dslash_ring_shape(const DslashArgs<float>& a, int warps, int slots, int ctas_per_sm,
+                                     cudaStream_t stream) {
+  if (ctas_per_sm == 2) return launch_dslash_ring_one<SELF, POST, NRHS, 224, 2>(a, warps, slots, stream);
+  if (warps > 8) return launch_dslash_ring_one<SELF, POST, NRHS, 512, 1>(a, warps, slots, stream);
+  return launch_dslash_ring_one<SELF, POST, NRHS, 256, 1>(a, warps, slots, stream);
+}
+
 template <int NRHS>
 cudaError_t launch_dslash_ring(const DslashArgs<float>& a, int self_mode, int post_mode, int warps, int slots,
-                               cudaStream_t stream) {
+                               int ctas_per_sm, cudaStream_t stream) {
   if (a.lay.nrhs != NRHS || a.lay.log_s != 0 || a.links_aos == nullptr) return cudaErrorInvalidValue;
-  if (warps < 1 || warps > 8 || slots < 1 || slots > 8) return cudaErrorInvalidValue;
-  if (ring::smem_bytes<NRHS>(warps, slots) > 227 * 1024) return cudaErrorInvalidValue;
+  if (warps < 1 || warps > 16 || slots < 1 || slots > 8 || ctas_per_sm < 1 || ctas_per_sm > 2)
+    return cudaErrorInvalidValue;
+  if ((size_t)ctas_per_sm * ring::smem_bytes<NRHS>(warps, slots) > 227 * 1024) return cudaErrorInvalidValue;
   if ((self_mode == SELF_BLOCK && a.blocks_aos == nullptr) ||
       (post_mode == POST_BLOCKINV && a.blocks_inv_aos == nullptr))
     return cudaErrorInvalidValue;
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE)
-    return launch_dslash_ring_one<SELF_SCALAR, POST_NONE, NRHS>(a, warps, slots, stream);
+    return launch_dslash_ring_shape<SELF_SCALAR, POST_NONE, NRHS>(a, warps, slots, ctas_per_sm, stream);
   if (self_mode == SELF_BLOCK && post_mode == POST_NONE)
-    return launch_dslash_ring_one<SELF_BLOCK, POST_NONE, NRHS>(a, warps, slots, stream);
+    return launch_dslash_ring_shape<SELF_BLOCK, POST_NONE, NRHS>(a, warps, slots, ctas_per_sm, stream);
   if (self_mode == SELF_NONE && post_mode == POST_SCALAR)
-    return launch_dslash_ring_one<SELF_NONE, POST_SCALAR, NRHS>(a, warps, slots, stream);
+    return launch_dslash_ring_shape<SELF_NONE, POST_SCALAR, NRHS>(a, warps, slots, ctas_per_sm, stream);
   if (self_mode == SELF_NONE && post_mode == POST_BLOCKINV)
-    return launch_dslash_ring_one<SELF_NONE, POST_BLOCKINV, NRHS>(a, warps, slots, stream);
+    return launch_dslash_ring_shape<SELF_NONE, POST_BLOCKINV, NRHS>(a, warps, slots, ctas_per_sm, stream);
   return cudaErrorInvalidValue;
 }
 
 #define LQCD_DSLASH_RING_TU(NRHS) \
-  template cudaError_t launch_dslash_ring<NRHS>(const DslashArgs<float>&, int, int, int, int, cudaStream_t);
+  template cudaError_t launch_dslash_ring<NRHS>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 
 }  // namespace lqcd

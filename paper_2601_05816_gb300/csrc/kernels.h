@@ -15,6 +15,14 @@ cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, 
 // Site-major FP32 copies for the ring hopping kernel: links [4][V][10] float2, blocks [V][72] float.
 cudaError_t launch_links_aos(int V, const void* links32, void* aos, cudaStream_t s);
 cudaError_t launch_blocks_aos(int V, const void* blk32, void* aos, cudaStream_t s);
+// Column map of the solver's compaction (at most 64 rhs).
+struct ColumnMap {
+  int col[64];
+};
+// Gather (dst column k <- src column map.col[k]) or scatter (dst column map.col[k] <- src
+// column k) between FP64 packed blocks of n_sites sites with layouts ls and ld.
+cudaError_t launch_repack_columns(int64_t n_sites, PackedLayout ls, PackedLayout ld, const ColumnMap& map,
+                                  bool scatter, const void* src, void* dst, cudaStream_t stream);
 cudaError_t launch_gauge_pack(const Geom& g, int time_bc, const void* U, void* l64, void* l32,
                               cudaStream_t stream);
 

@@ -87,6 +87,38 @@ cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, 
   return cudaGetLastError();
 }
 
+// Column repacking between two FP64 packed blocks of the same sites with different
+// rhs counts (the solver's compaction of its active rhs): gather
+//   dst(layout nd)[i][c][k] = src(layout ns)[i][c][map[k]],  k < nd,
+// or scatter
+//   dst(layout nd)[i][c][map[k]] = src(layout ns)[i][c][k],  k < ns.
+__global__ void repack_columns_kernel(int64_t n_sites, PackedLayout ls, PackedLayout ld, ColumnMap map,
+                                      bool scatter, const double2* __restrict__ src, double2* __restrict__ dst) {
+  const int nk = scatter ? ls.nrhs : ld.nrhs;
+  const int64_t total = n_sites * 12 * nk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % nk);
+    const int64_t q = e / nk;
+    const int c = (int)(q % 12);
+    const int64_t i = q / 12;
+    if (scatter) dst[ld.index(i, c, map.col[k])] = src[ls.index(i, c, k)];
+    else dst[ld.index(i, c, k)] = src[ls.index(i, c, map.col[k])];
+  }
+}
+
+cudaError_t launch_repack_columns(int64_t n_sites, PackedLayout ls, PackedLayout ld, const ColumnMap& map,
+                                  bool scatter, const void* src, void* dst, cudaStream_t stream) {
+  const int nk = scatter ? ls.nrhs : ld.nrhs;
+  const int64_t total = n_sites * 12 * nk;
+  const int threads = 256;
+  const int64_t b = (total + threads - 1) / threads;
+  const int blocks = (int)(b > 65535 * 16 ? 65535 * 16 : (b < 1 ? 1 : b));
+  repack_columns_kernel<<<blocks, threads, 0, stream>>>(n_sites, ls, ld, map, scatter, (const double2*)src,
+                                                        (double2*)dst);
+  return cudaGetLastError();
+}
+
 // Canonical U [V][4][3][3] complex128 -> packed [4][9][V] in FP64 and FP32, eo site order.
 __global__ void gauge_pack_kernel(Geom g, int time_bc, const double2* __restrict__ U,
                                   double2* __restrict__ l64, float2* __restrict__ l32) {

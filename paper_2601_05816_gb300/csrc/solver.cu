@@ -658,6 +658,7 @@ struct SolveJob {
   std::chrono::steady_clock::time_point t0;
   bool eo = false, f64_inner = false, bf16 = false, reorth = true;
   int m = 0;
+  int ortho_req = 1;
   double inner_tol = 0.0;
   int64_t n_full = 0, n_half = 0, n_sys = 0;
   size_t full64 = 0;
@@ -688,9 +689,23 @@ struct SolveJob {
   long long nl = 0;  // kernel launches of this solve
   double op_bytes_inner = 0.0;
   lqcd_status result = LQCD_NOT_CONVERGED;
+  // compaction of the active rhs (params.compact): the solve runs on nrhs columns of the
+  // caller's nrhs0; col[k] is the caller's column of current column k, b_cur / x_cur the
+  // FP64 packed full blocks of the current columns (b64 / x64, the caller's, before any
+  // compaction). x64 keeps every caller column's latest solution.
+  int nrhs0 = 0;
+  std::vector<int> col;
+  void *b_cur = nullptr, *x_cur = nullptr;
+  std::vector<int> iters0;
+  std::vector<double> bnorm0;
+  int compactions = 0;
 
   lqcd_status setup(lqcd_ctx c, const lqcd_solve_params* params, int nr, const void* bb, void* xx,
                     lqcd_solve_stats* st_out, cudaStream_t stream);
+  // buffers, plans and the system right-hand side for the current column count
+  lqcd_status configure();
+  // keep only the current columns listed in keep (at an FP64 restart)
+  lqcd_status compact(const std::vector<int>& keep);
   lqcd_status enqueue_residual();
   // after the stream has been synchronised: *run = a cycle follows; with neither run
   // nor finished, the next residual (the FP64 one) is due before the next cycle
@@ -723,7 +738,7 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
   bf16 = P.precision == LQCD_BF16S;
   m = P.restart_len;
   reorth = P.reorth != 0 || bf16;
-  const int ortho_req = P.reorth == 0 ? (bf16 ? 1 : 0) : (P.reorth == 2 ? 2 : 1);
+  ortho_req = P.reorth == 0 ? (bf16 ? 1 : 0) : (P.reorth == 2 ? 2 : 1);
   inner_tol = P.inner_tol > 0.0 ? P.inner_tol : (f64_inner ? 0.0 : 1e-4);
   n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
   n_half = n_full / 2;
@@ -768,6 +783,62 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     if ((st = workspace(ctx, "solve_e32", (size_t)n_sys * sizeof(float2), &e32)) != LQCD_OK) return st;
     if ((st = workspace(ctx, "solve_t32", (size_t)n_sys * sizeof(float2), &t32)) != LQCD_OK) return st;
   }
+  if ((st = workspace(ctx, "solve_beta0", sizeof(double) * nrhs, (void**)&d_beta0)) != LQCD_OK) return st;
+  if ((st = pinned_staging(ctx, sizeof(Staging), (void**)&hs)) != LQCD_OK) return st;
+  prof.on = P.profile != 0;
+  if (prof.on) {
+    if (ctx->prof_events.empty()) {
+      ctx->prof_events.resize(4 * 64);
+      for (auto& e : ctx->prof_events) LQCD_CUDA(cudaEventCreate(&e), "event create");
+    }
+    prof.ev = ctx->prof_events;
+  }
+
+  // ---------------- inputs
+  if (b_host) LQCD_CUDA(cudaMemcpyAsync(b_can, b, full64, cudaMemcpyHostToDevice, s), "upload b");
+  if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, b_can, b64, s)) != LQCD_OK) return st;
+  const int log_s = layout_for(ctx, nrhs).log_s;
+  // adjoint system: D^dagger x = b is solved as D y = gamma5 b, x = gamma5 y
+  if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, b64, s), "gamma5 b");
+  if (P.x0_given) {
+    if (x_host) LQCD_CUDA(cudaMemcpyAsync(x_can, x, full64, cudaMemcpyHostToDevice, s), "upload x0");
+    if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x_can, x64, s)) != LQCD_OK) return st;
+    if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, x64, s), "gamma5 x0");
+  } else {
+    LQCD_CUDA(cudaMemsetAsync(x64, 0, full64, s), "zero x");
+  }
+  plan_full = blas_plan(n_full, nrhs, ctx->num_sms);
+  if ((st = workspace(ctx, "solve_partials_full", sizeof(double2) * (size_t)nrhs * plan_full.blocks,
+                      &red_partials)) != LQCD_OK)
+    return st;
+  if ((st = workspace(ctx, "solve_hn", sizeof(double2) * (size_t)(m + 1) * nrhs, &B.hn)) != LQCD_OK) return st;
+  LQCD_CUDA(launch_norm2(true, plan_full, n_full, b64, red_partials, B.hn, s), "norm b");
+  nl += (P.x0_given ? 2 : 1) + 2;  // packs, norm + reduction
+  LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read norm b");
+  LQCD_CUDA(cudaStreamSynchronize(s), "sync");
+  bnorm0.assign(nrhs, 0.0);
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm0[r] = std::sqrt(hs->rn2[2 * r]);
+    if (!std::isfinite(bnorm0[r]))
+      return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: right-hand side %d is not finite", r);
+  }
+  nrhs0 = nrhs;
+  col.resize(nrhs);
+  for (int r = 0; r < nrhs; ++r) col[r] = r;
+  iters0.assign(nrhs, 0);
+  b_cur = b64;
+  x_cur = x64;
+  return configure();
+}
+
+lqcd_status SolveJob::configure() {
+  lqcd_status st;
+  n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
+  n_half = n_full / 2;
+  n_sys = eo ? n_half : n_full;
+  B.nrhs = nrhs;
+  B.n_sys = n_sys;
+  B.inner_bytes = (size_t)n_sys * (f64_inner ? sizeof(double2) : (bf16 ? sizeof(__nv_bfloat162) : sizeof(float2)));
   rn_prev.assign(nrhs, 0.0);
   active_outer.assign(nrhs, 0);
   inner_done.assign(nrhs, 1);
@@ -799,7 +870,7 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     B.dc.nu = (double*)take();
     B.dc.g = (double2*)take();
     B.dc.ctr = (unsigned*)take();
-    LQCD_CUDA(cudaMemsetAsync(B.dc.ctr, 0, 2 * sizeof(unsigned), stream), "dcgs counters");
+    LQCD_CUDA(cudaMemsetAsync(B.dc.ctr, 0, 2 * sizeof(unsigned), s), "dcgs counters");
   }
   const size_t hb = sizeof(double2) * (size_t)(m + 1) * nrhs;
   if ((st = workspace(ctx, "solve_partials", hb * B.plan.blocks, &B.partials)) != LQCD_OK) return st;
@@ -834,55 +905,48 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     B.st.all_done = (int*)take();
     B.st.kmax = (int*)take();
   }
-  if ((st = workspace(ctx, "solve_beta0", sizeof(double) * nrhs, (void**)&d_beta0)) != LQCD_OK) return st;
-  if ((st = pinned_staging(ctx, sizeof(Staging), (void**)&hs)) != LQCD_OK) return st;
-  prof.on = P.profile != 0;
-  if (prof.on) {
-    if (ctx->prof_events.empty()) {
-      ctx->prof_events.resize(4 * 64);
-      for (auto& e : ctx->prof_events) LQCD_CUDA(cudaEventCreate(&e), "event create");
-    }
-    prof.ev = ctx->prof_events;
-  }
-
-  // ---------------- inputs
-  if (b_host) LQCD_CUDA(cudaMemcpyAsync(b_can, b, full64, cudaMemcpyHostToDevice, s), "upload b");
-  if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, b_can, b64, s)) != LQCD_OK) return st;
-  const int log_s = layout_for(ctx, nrhs).log_s;
-  // adjoint system: D^dagger x = b is solved as D y = gamma5 b, x = gamma5 y
-  if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, b64, s), "gamma5 b");
-  if (P.x0_given) {
-    if (x_host) LQCD_CUDA(cudaMemcpyAsync(x_can, x, full64, cudaMemcpyHostToDevice, s), "upload x0");
-    if ((st = lqcd_pack(ctx, LQCD_C128, LQCD_SITES_FULL, nrhs, x_can, x64, s)) != LQCD_OK) return st;
-    if (P.dagger) LQCD_CUDA(launch_gamma5_packed(n_full, nrhs, log_s, x64, s), "gamma5 x0");
-  } else {
-    LQCD_CUDA(cudaMemsetAsync(x64, 0, full64, s), "zero x");
-  }
-  plan_full = blas_plan(n_full, nrhs, ctx->num_sms);
-  if ((st = workspace(ctx, "solve_partials_full", sizeof(double2) * (size_t)nrhs * plan_full.blocks,
-                      &red_partials)) != LQCD_OK)
-    return st;
-  LQCD_CUDA(launch_norm2(true, plan_full, n_full, b64, red_partials, B.hn, s), "norm b");
-  nl += (P.x0_given ? 2 : 1) + 2 + (eo ? 2 : 0);  // packs, norm + reduction, prepare
-  LQCD_CUDA(cudaMemcpyAsync(hs->rn2, B.hn, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, s), "read norm b");
-  LQCD_CUDA(cudaStreamSynchronize(s), "sync");
   bnorm.assign(nrhs, 0.0);
-  for (int r = 0; r < nrhs; ++r) {
-    bnorm[r] = std::sqrt(hs->rn2[2 * r]);
-    if (!std::isfinite(bnorm[r]))
-      return set_error(LQCD_ERR_NONFINITE, "lqcd_solve: right-hand side %d is not finite", r);
-  }
-  sys_b = b64;
-  sys_x = x64;
+  for (int r = 0; r < nrhs; ++r) bnorm[r] = bnorm0[col[r]];
+  sys_b = b_cur;
+  sys_x = x_cur;
   if (eo) {
-    if ((st = schur_prepare(ctx, true, nrhs, b64, bhat, tmp64, s)) != LQCD_OK) return st;
+    if ((st = schur_prepare(ctx, true, nrhs, b_cur, bhat, tmp64, s)) != LQCD_OK) return st;
     sys_b = bhat;
-    sys_x = (char*)x64 + (size_t)n_half * sizeof(double2);
+    sys_x = (char*)x_cur + (size_t)n_half * sizeof(double2);
+    nl += 2;
   }
   iters.assign(nrhs, 0);
   relres.assign(nrhs, 0.0);
   op_bytes_inner = op_algorithmic_bytes(ctx, P.op, f64_inner, nrhs, bf16);
   return LQCD_OK;
+}
+
+lqcd_status SolveJob::compact(const std::vector<int>& keep) {
+  const int n2 = (int)keep.size();
+  const int64_t V = ctx->g.V;
+  const PackedLayout L0 = layout_for(ctx, nrhs0), Lc = layout_for(ctx, nrhs), L2 = layout_for(ctx, n2);
+  ColumnMap mp;
+  if (x_cur != x64) {  // the caller's block gets the latest solution of every current column
+    for (int k = 0; k < nrhs; ++k) mp.col[k] = col[k];
+    LQCD_CUDA(launch_repack_columns(V, Lc, L0, mp, true, x_cur, x64, s), "compaction scatter x");
+  }
+  std::vector<int> next(n2);
+  for (int k = 0; k < n2; ++k) next[k] = mp.col[k] = col[keep[k]];
+  const size_t bytes2 = (size_t)packed_elems(ctx, LQCD_SITES_FULL, n2) * sizeof(double2);
+  lqcd_status st;
+  void *bc, *xc;
+  if ((st = workspace(ctx, "solve_b_compact", bytes2, &bc)) != LQCD_OK) return st;
+  if ((st = workspace(ctx, "solve_x_compact", bytes2, &xc)) != LQCD_OK) return st;
+  LQCD_CUDA(launch_repack_columns(V, L0, L2, mp, false, b64, bc, s), "compaction gather b");
+  LQCD_CUDA(launch_repack_columns(V, L0, L2, mp, false, x64, xc, s), "compaction gather x");
+  nl += (x_cur != x64 ? 1 : 0) + 2;
+  for (int k = 0; k < nrhs; ++k) iters0[col[k]] += iters[k];
+  col = next;
+  nrhs = n2;
+  b_cur = bc;
+  x_cur = xc;
+  ++compactions;
+  return configure();
 }
 
 // The residual of the next restart and its norms, copied to the pinned staging area:
@@ -964,6 +1028,18 @@ lqcd_status SolveJob::decide(bool* run) {
       finished = true;
       return LQCD_OK;
     }
+    if (P.compact && nrhs - n_active >= std::max(1, nrhs / 8)) {
+      // retire the converged rhs from the block: the solve continues on the active
+      // columns only, so the operator and Gram-Schmidt move fewer bytes; the FP64
+      // residual of the compacted block is computed next
+      std::vector<int> keep;
+      for (int r = 0; r < nrhs; ++r)
+        if (active_outer[r]) keep.push_back(r);
+      lqcd_status st = compact(keep);
+      if (st != LQCD_OK) return st;
+      outer_next = true;
+      return LQCD_OK;
+    }
     outer_next = false;
     inner_cycles = 0;
   } else {
@@ -1020,6 +1096,22 @@ lqcd_status SolveJob::enqueue_cycle(cudaStream_t cs, bool allow_graph) {
 // Reconstruct x_e (odd-even), final full-operator residual, unpack and download x, stats.
 lqcd_status SolveJob::finish() {
   lqcd_status st;
+  if (x_cur != x64) {  // compacted: the last columns' solutions go back to the caller's block
+    ColumnMap mp;
+    for (int k = 0; k < nrhs; ++k) mp.col[k] = col[k];
+    LQCD_CUDA(launch_repack_columns(ctx->g.V, layout_for(ctx, nrhs), layout_for(ctx, nrhs0), mp, true, x_cur, x64, s),
+              "compaction scatter x");
+    nl += 1;
+  }
+  for (int k = 0; k < nrhs; ++k) iters0[col[k]] += iters[k];
+  // the rest runs on the caller's nrhs0 columns
+  nrhs = nrhs0;
+  n_full = (int64_t)packed_elems(ctx, LQCD_SITES_FULL, nrhs);
+  n_half = n_full / 2;
+  iters = iters0;
+  bnorm = bnorm0;
+  relres.assign(nrhs, 0.0);
+  sys_x = eo ? (void*)((char*)x64 + (size_t)n_half * sizeof(double2)) : x64;
   if (eo && (st = schur_reconstruct(ctx, true, nrhs, b64, sys_x, x64, s)) != LQCD_OK) return st;
   if ((st = apply_operator(ctx, LQCD_OP_FULL, true, nrhs, x64, t64, nullptr, nullptr, s)) != LQCD_OK) return st;
   LQCD_CUDA(launch_sub_norm(plan_full, n_full, b64, t64, r64, red_partials, B.hn, s), "final residual");
@@ -1182,6 +1274,7 @@ lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_pa
       running[i] = run ? 1 : 0;
       n_run += run;
       key += run ? '1' : '0';
+      key += std::to_string(jobs[i].compactions) + ',';   // a compacted lattice's branch is captured anew
     }
     bool all_finished = true;
     for (auto& j : jobs) all_finished = all_finished && j.finished;

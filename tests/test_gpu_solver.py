@@ -341,3 +341,50 @@ def test_near_breakdown_plane_wave_solve(precision, op, reorth):
     else:
         assert res.iterations <= 64, res.iters_per_rhs
     lat.close()
+
+
+@pytest.mark.parametrize("precision", [lq.C64, lq.C128])
+@pytest.mark.parametrize("op", [lq.OP_SCHUR, lq.OP_FULL])
+def test_retirement_compacts_the_active_rhs(precision, op):
+    """Eight rhs of uneven difficulty: rhs 0-1 start at the oracle's solution (retired at the first
+    restart), rhs 2-3 near it (relative error 1e-6: they retire after a few cycles), rhs 4-7 from zero.
+    With compaction the retired rhs leave the block (the operator then runs on fewer rhs, so its
+    algorithmic bytes per launch fall); every rhs still meets the tolerance with the oracle's operator,
+    the immediately retired ones keep their initial guess exactly, and the solutions agree with those
+    of the solve without compaction."""
+    dims = (8, 4, 4, 8)
+    m0, c_sw, nrhs = -0.1, 1.0, 8
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1301)
+    b = syn.gaussian_spinors(dims, nrhs, 1302)
+    A, Ainv = oracle.diag_blocks(U, m0, c_sw)
+    xo, _ = oracle.solve_eo(U, A, Ainv, b[:4], tol=1e-13, m=40, max_restarts=200)
+    rng = np.random.default_rng(1303)
+    x0 = np.zeros_like(b)
+    x0[:2] = xo[:2]
+    noise = rng.standard_normal(xo[2:4].shape) + 1j * rng.standard_normal(xo[2:4].shape)
+    x0[2:4] = xo[2:4] + 1e-6 * noise * (np.linalg.norm(xo[2:4]) / np.linalg.norm(noise))
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    out = {}
+    for compact in (True, False):
+        x = torch.from_numpy(x0.copy()).cuda()
+        res = lat.solve(torch.from_numpy(b).cuda(), x, nrhs, op=op, precision=precision, restart_len=16,
+                        tol=1e-10, x0_given=True, profile=True, compact=compact, max_restarts=400)
+        torch.cuda.synchronize()
+        assert res.status == lq.OK, (compact, res)
+        xs = x.cpu().numpy()
+        rel = oracle_relres(U, m0, c_sw, b, xs)
+        assert np.all(rel <= 1e-10), (compact, rel)
+        out[compact] = (res, xs)
+    rc, xc = out[True]
+    rn, xn = out[False]
+    # immediately retired rhs: untouched
+    assert np.array_equal(xc[:2], x0[:2])
+    # fewer iterations for the rhs that started near the solution
+    assert max(rc.iters_per_rhs[:4]) < min(rc.iters_per_rhs[4:]), rc.iters_per_rhs
+    # bytes per operator launch fall once rhs retire (the non-compacting solve keeps all 8)
+    assert rc.op_bytes / rc.op_launches < rn.op_bytes / rn.op_launches
+    for k in range(nrhs):
+        assert np.linalg.norm(xc[k] - xn[k]) <= 1e-6 * np.linalg.norm(xn[k]), k
+    lat.close()
