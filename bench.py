@@ -285,6 +285,16 @@ def run_reference(args, w):
 
 # ------------------------------------------------------------------ GPU arm
 
+def op_bytes(V, nrhs, dtype_bytes, op, link_bytes):
+    """Algorithmic bytes of one apply: spinors once per pass, each link (link_bytes) and site block
+    (72 reals) once per pass. Full: (48 b s + 4 L + 72 s) per site; Schur: (120 b s + 16 L + 144 s)
+    per odd site (two passes, each reading all 4V links)."""
+    s = dtype_bytes
+    if op == "full":
+        return V * (48 * nrhs * s + 4 * link_bytes + 72 * s)
+    return (V // 2) * (120 * nrhs * s + 16 * link_bytes + 144 * s)
+
+
 def dslash_point(lat, lq, torch, dims, nrhs, dtype, op, reps, flush):
     V = dims[0] * dims[1] * dims[2] * dims[3]
     sites = lq.SITES_FULL if op == lq.OP_FULL else lq.SITES_ODD
@@ -306,13 +316,14 @@ def dslash_point(lat, lq, torch, dims, nrhs, dtype, op, reps, flush):
         times.append(e0.elapsed_time(e1) * 1e-3)
     t = statistics.median(times)
     sz = 8 if dtype == lq.C128 else 4
-    if op == lq.OP_FULL:
-        nbytes = V * (48 * nrhs + 144) * sz
-        units = V * nrhs
+    if lat.link_storage() == lq.LINKS_BF16 and dtype != lq.C128:
+        link_bytes = 12 * 2
     else:
-        nbytes = (V // 2) * (120 * nrhs + 432) * sz
-        units = (V // 2) * nrhs
-    return t, nbytes, units
+        link_bytes = lat.variant_link_reals(dtype, lat.kernel_variant(dtype, nrhs, op)) * sz
+    name = "full" if op == lq.OP_FULL else "schur"
+    nbytes = op_bytes(V, nrhs, sz, name, link_bytes)
+    units = V * nrhs if op == lq.OP_FULL else (V // 2) * nrhs
+    return t, nbytes, units, link_bytes
 
 
 def run_kernel_workload(args, w):
@@ -703,16 +714,31 @@ def extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line):
         for dt in (lq.C64, lq.C128):
             lat.tune(dt, nr, reps=3)
             for op in (lq.OP_SCHUR, lq.OP_FULL):
-                tt, nb, units = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
+                tt, nb, units, lb = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
                 sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
                               "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
-                              "variant": lat.kernel_variant(dt, nr, op),
+                              "variant": lat.kernel_variant(dt, nr, op), "link_bytes": lb,
                               "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
                               "site_rhs_per_s": units / tt})
+    # BF16 two-row link storage (the FP32 operator with links rounded to BF16) at small rhs counts,
+    # where the links are the largest share of the bytes
+    bf16_links = []
+    lat.set_link_storage(lq.LINKS_BF16)
+    for nr in [v for v in nr_list if v <= 8]:
+        for op in (lq.OP_SCHUR, lq.OP_FULL):
+            tt, nb, units, lb = dslash_point(lat, lq, torch, dims, nr, lq.C64, op, args.dslash_reps, flush)
+            ref = next(p for p in sweep if p["nrhs"] == nr and p["dtype"] == "c64" and
+                       p["op"] == ("schur" if op == lq.OP_SCHUR else "full"))
+            bf16_links.append({"nrhs": nr, "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
+                               "link_bytes": lb, "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
+                               "site_rhs_per_s": units / tt, "speedup_vs_fp32_links": ref["ms"] / (tt * 1e3)})
+    lat.set_link_storage(lq.LINKS_FP32)
     del flush
-    line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48b+144)s/site, "
-                      "schur (120b+432)s/odd site", "l2_flush": "512 MB memset between applies",
-                      "applies_per_point": args.dslash_reps, "statistic": "median", "points": sweep}
+    line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48 b s + 4 L + 72 s) per site, "
+                      "schur (120 b s + 16 L + 144 s) per odd site; L = bytes per link read (18 or 12 reals)",
+                      "l2_flush": "512 MB memset between applies",
+                      "applies_per_point": args.dslash_reps, "statistic": "median", "points": sweep,
+                      "bf16_two_row_links": bf16_links}
 
 
 def extras_gmres(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, inner, results, line):

@@ -168,8 +168,27 @@ lqcd_status lqcd_tune(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, int reps, double
  * saved tuning cache; -1 restores the default). LQCD_ERR_ARG if the variant does
  * not fit nrhs (rhs per thread must divide nrhs). No GPU work. */
 int lqcd_kernel_variant_count(lqcd_dtype dtype);
+/* Reals per link a launch variant reads (18, or 12 for the two-row copy whose third row the
+ * kernel rebuilds; either way the same operator to rounding); -1 on bad arguments. */
+int lqcd_kernel_variant_link_reals(lqcd_dtype dtype, int variant);
 int lqcd_get_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op);
 lqcd_status lqcd_set_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op, int variant);
+
+/* Link storage of the FP32 operator (Sec. III-A-1 stores U_mu(x) as a row-major 3x3
+ * matrix; the BF16 form is the precision extension of the mixed solver, not in the paper):
+ *   LQCD_LINKS_FP32 (default): FP32 links (18 reals, or the exact two-row copy with the
+ *     third row rebuilt where the autotuner picks such a variant);
+ *   LQCD_LINKS_BF16: rows 0 and 1 of every link rounded to BF16 (12 reals, 24 bytes), the
+ *     third row rebuilt in FP32 as conj(row0 x row1) and multiplied by the time boundary
+ *     factor on the last time slice. This changes the operator by O(2^-9) relative: it
+ *     applies to lqcd_apply_packed / lqcd_apply with LQCD_C64 or LQCD_BF16S and to the
+ *     FP32 inner operator of lqcd_solve (whose FP64 residual, on the FP64 links, still
+ *     decides convergence); FP64 applies are unaffected. The clover blocks stay FP64-built.
+ * Takes effect for the next call; no GPU work. LQCD_ERR_ARG for an unknown format. */
+enum { LQCD_LINKS_FP32 = 0, LQCD_LINKS_BF16 = 1 };
+lqcd_status lqcd_set_link_storage(lqcd_ctx ctx, int format);
+/* The context's link storage (LQCD_LINKS_*), -1 for a null context. */
+int lqcd_get_link_storage(lqcd_ctx ctx);
 
 /* Odd-even source preparation and solution reconstruction (Sec. III-A-2),
  * packed layout, full-lattice blocks hold even then odd sites:

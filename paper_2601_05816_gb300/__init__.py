@@ -20,6 +20,7 @@ OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_SINGULAR, ERR_STATE = -1, -2, -3, -4, -5, -6
 C64, C128, BF16S = 1, 2, 3
 OP_FULL, OP_SCHUR = 0, 1
+LINKS_FP32, LINKS_BF16 = 0, 1
 SITES_FULL, SITES_EVEN, SITES_ODD = 0, 1, 2
 
 _lib = None
@@ -79,6 +80,9 @@ _SIGS = {
     "lqcd_kernel_variant_count": (_I, [_I]),
     "lqcd_get_kernel_variant": (_I, [_VP, _I, _I, _I]),
     "lqcd_set_kernel_variant": (_I, [_VP, _I, _I, _I, _I]),
+    "lqcd_set_link_storage": (_I, [_VP, _I]),
+    "lqcd_kernel_variant_link_reals": (_I, [_I, _I]),
+    "lqcd_get_link_storage": (_I, [_VP]),
 }
 
 
@@ -254,12 +258,23 @@ class Lattice:
                                    _stream(stream)), "lqcd_tune")
         return [(times[2 * v], times[2 * v + 1]) for v in range(n.value)]
 
+    def variant_link_reals(self, dtype: int, variant: int) -> int:
+        """Reals per link read by a hopping-kernel launch variant (18, or 12 with the third row rebuilt)."""
+        return int(self._lib.lqcd_kernel_variant_link_reals(int(dtype), int(variant)))
+
     def kernel_variant(self, dtype: int, nrhs: int, op: int) -> int:
         return int(self._lib.lqcd_get_kernel_variant(self._h, int(dtype), int(nrhs), int(op)))
 
     def set_kernel_variant(self, dtype: int, nrhs: int, op: int, variant: int):
         _check(self._lib.lqcd_set_kernel_variant(self._h, int(dtype), int(nrhs), int(op), int(variant)),
                "lqcd_set_kernel_variant")
+
+    def set_link_storage(self, fmt: int):
+        """Link storage of the FP32 operator: LINKS_FP32 (default) or LINKS_BF16 (two rows in BF16)."""
+        _check(self._lib.lqcd_set_link_storage(self._h, int(fmt)), "lqcd_set_link_storage")
+
+    def link_storage(self) -> int:
+        return int(self._lib.lqcd_get_link_storage(self._h))
 
     def save_tuning(self, path: str, keys):
         """Write the chosen variants for keys = [(dtype, nrhs, op), ...] to a JSON cache."""

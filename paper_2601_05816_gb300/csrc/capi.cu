@@ -121,7 +121,11 @@ static DslashArgs<Real> base_args(lqcd_ctx ctx, int nrhs, bool f64) {
     a.links_aos = ctx->links32_aos;
     a.blocks_aos = ctx->blk32_aos;
     a.blocks_inv_aos = ctx->inv32_aos;
+    a.links_r12 = ctx->links32_r12;
+    a.links_r12_bf16 = ctx->links_bf16_r12;
+    a.link_format = ctx->link_format == LQCD_LINKS_BF16 ? 2 : 0;
   }
+  a.time_bc = (Real)ctx->time_bc;
   a.err = ctx->ws.count("wait_flag") ? (int*)ctx->ws["wait_flag"].p : nullptr;
   return a;
 }
@@ -358,6 +362,7 @@ lqcd_status lqcd_free(lqcd_ctx ctx) {
   free_ptr(ctx->links64); free_ptr(ctx->links32);
   free_ptr(ctx->blk64); free_ptr(ctx->inv64); free_ptr(ctx->blk32); free_ptr(ctx->inv32);
   free_ptr(ctx->links32_aos); free_ptr(ctx->blk32_aos); free_ptr(ctx->inv32_aos);
+  free_ptr(ctx->links32_r12); free_ptr(ctx->links_bf16_r12);
   void* e = ctx->d_err; free_ptr(e);
   for (auto& kv : ctx->ws) free_ptr(kv.second.p);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -378,6 +383,8 @@ lqcd_status lqcd_set_gauge(lqcd_ctx ctx, const void* U, void* stream) {
     LQCD_CUDA(cudaMalloc(&ctx->links32, 36 * V * sizeof(float2)), "cudaMalloc(links32)");
     LQCD_CUDA(cudaMalloc((void**)&ctx->d_err, sizeof(int)), "cudaMalloc(err)");
     LQCD_CUDA(cudaMalloc(&ctx->links32_aos, 40 * V * sizeof(float2)), "cudaMalloc(links32 site-major)");
+    LQCD_CUDA(cudaMalloc(&ctx->links32_r12, 24 * V * sizeof(float2)), "cudaMalloc(links32 two rows)");
+    LQCD_CUDA(cudaMalloc(&ctx->links_bf16_r12, 24 * V * sizeof(__nv_bfloat162)), "cudaMalloc(links bf16 two rows)");
     if (wait_flag(ctx) == nullptr) return set_error(LQCD_ERR_OOM, "lqcd_set_gauge: cannot allocate the wait flag");
   }
   const void* src = U;
@@ -391,6 +398,7 @@ lqcd_status lqcd_set_gauge(lqcd_ctx ctx, const void* U, void* stream) {
   }
   LQCD_CUDA(launch_gauge_pack(ctx->g, ctx->time_bc, src, ctx->links64, ctx->links32, s), "gauge pack");
   LQCD_CUDA(launch_links_aos(ctx->g.V, ctx->links32, ctx->links32_aos, s), "links site-major");
+  LQCD_CUDA(launch_links_r12(ctx->g.V, ctx->links32, ctx->links32_r12, ctx->links_bf16_r12, s), "links two rows");
   if (src != U) LQCD_CUDA(cudaStreamSynchronize(s), "gauge upload sync");
   ctx->have_gauge = true;
   ctx->have_blocks = false;
@@ -565,6 +573,28 @@ int lqcd_get_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op
 int lqcd_kernel_variant_count(lqcd_dtype dtype) {
   if (!valid_dtype(dtype)) return 0;
   return dslash_variant_count(dtype == LQCD_C128);
+}
+
+lqcd_status lqcd_set_link_storage(lqcd_ctx ctx, int format) {
+  CHECK_CTX(ctx);
+  if (format != LQCD_LINKS_FP32 && format != LQCD_LINKS_BF16)
+    return set_error(LQCD_ERR_ARG, "lqcd_set_link_storage: unknown format %d", format);
+  ctx->link_format = format;
+  if (ctx->cycle.exec) {  // a captured solver cycle holds the previous kernels
+    cudaGraphExecDestroy(ctx->cycle.exec);
+    cudaGraphDestroy(ctx->cycle.graph);
+    ctx->cycle.exec = nullptr;
+    ctx->cycle.graph = nullptr;
+    ctx->cycle.key.clear();
+  }
+  return LQCD_OK;
+}
+
+int lqcd_get_link_storage(lqcd_ctx ctx) { return ctx ? ctx->link_format : -1; }
+
+int lqcd_kernel_variant_link_reals(lqcd_dtype dtype, int variant) {
+  if (!valid_dtype(dtype) || variant < 0 || variant >= dslash_variant_count(dtype == LQCD_C128)) return -1;
+  return dslash_variant(dtype == LQCD_C128, variant).links == 1 ? 12 : 18;
 }
 
 lqcd_status lqcd_tune(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, int reps, double* times_ms, int* n_variants,

@@ -43,6 +43,9 @@ struct lqcd_ctx_s {
   void* links32_aos = nullptr;  // [4][V][10] float2, links padded to 80 bytes (ring kernel)
   void* blk32_aos = nullptr;    // [V][72] float, A per site (ring kernel)
   void* inv32_aos = nullptr;    // [V][72] float, A^{-1} per site (ring kernel)
+  void* links32_r12 = nullptr;  // [4][6][V] float2, rows 0 and 1 of each link
+  void* links_bf16_r12 = nullptr;  // [4][6][V] BF16 pairs, the same rows rounded
+  int link_format = 0;          // FP32 operator links: LQCD_LINKS_FP32 (0) or LQCD_LINKS_BF16 (1)
   int* d_err = nullptr;     // device status bitmask
   std::map<std::string, lqcd::Buffer> ws;
   cudaStream_t capture_stream = nullptr;

@@ -62,6 +62,12 @@ struct DslashArgs {
   const void* blocks_inv_aos;  // [V][72] float: A(x)^{-1}
   int* err;                    // set (bit 0) when a bounded pipeline wait gives up
   int ring_slots;              // ring kernel: slots per warp (set by its launcher)
+  // two-row ("12-real") link copies for FP32 arithmetic, the third row rebuilt in the kernel
+  // as conj(row0 x row1) and then multiplied by the time boundary factor where it was folded in:
+  const void* links_r12;       // [4][6][V] float2: rows 0, 1 of each packed link
+  const void* links_r12_bf16;  // [4][6][V] BF16 pairs: the same rows rounded to BF16
+  int link_format;             // 0: 18-real FP32 links (links); 2: 12-real BF16 (links_r12_bf16)
+  Real time_bc;                // fermion time boundary factor (+1 / -1)
 };
 
 // NR complex numbers (NR consecutive rhs of one component).
@@ -238,9 +244,39 @@ __device__ __forceinline__ int64_t lidx(const PackedLayout& lay, int64_t i, int 
   else return lay.index(i, c, r);
 }
 
+// Link storage formats of the FP32 kernels: LF = 0 the 18-real links; LF = 1 rows 0 and 1
+// in FP32; LF = 2 rows 0 and 1 in BF16. For LF > 0 the third row of the SU(3) matrix is
+// rebuilt as conj(row0 x row1); the stored rows carry the time boundary factor b of
+// U_0 on the last time slice, which cancels in the cross product (b^2 = 1), so the
+// rebuilt row is multiplied by b for those links.
+__device__ __forceinline__ float2 cmul_f(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void rebuild_third_row(float2 u[9], float b) {
+  const float2 a0 = cmul_f(u[1], u[5]), a1 = cmul_f(u[2], u[4]);
+  const float2 b0 = cmul_f(u[2], u[3]), b1 = cmul_f(u[0], u[5]);
+  const float2 c0 = cmul_f(u[0], u[4]), c1 = cmul_f(u[1], u[3]);
+  u[6] = make_float2(b * (a0.x - a1.x), -b * (a0.y - a1.y));
+  u[7] = make_float2(b * (b0.x - b1.x), -b * (b0.y - b1.y));
+  u[8] = make_float2(b * (c0.x - c1.x), -b * (c0.y - c1.y));
+}
+template <int LF>
+__device__ __forceinline__ void load_link_r12(const DslashArgs<float>& a, int mu, int link_site, float2 u[9]) {
+  if constexpr (LF == 1) {
+    const float2* lp = static_cast<const float2*>(a.links_r12) + (int64_t)(mu * 6) * a.g.V + link_site;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) u[e] = __ldg(lp + (int64_t)e * a.g.V);
+  } else {
+    const __nv_bfloat162* lp =
+        static_cast<const __nv_bfloat162*>(a.links_r12_bf16) + (int64_t)(mu * 6) * a.g.V + link_site;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) u[e] = __bfloat1622float2(__ldg(lp + (int64_t)e * a.g.V));
+  }
+}
+
 // One hopping direction with direct (register) loads of the link and the neighbour
 // (BATCH: as one batch of volatile loads).
-template <typename Real, int NR, int MU, int DIR, bool BATCH, typename HIN, int NRHS = 0>
+template <typename Real, int NR, int MU, int DIR, bool BATCH, typename HIN, int NRHS = 0, int LF = 0>
 __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& c, int p, int r0,
                                         const HIN* hin, MC<Real, NR> acc[12]) {
   using C = typename Cplx<Real>::T;
@@ -251,7 +287,18 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<Real>& a, const Coord& 
   const C* lp = a.links + (int64_t)(MU * 9) * a.g.V + link_site;
   C u[9];
   MC<Real, NR> up[6], dn[6];
-  if constexpr (BATCH) {
+  if constexpr (LF > 0) {
+    static_assert(sizeof(Real) == 4, "two-row links: FP32 kernels only");
+    load_link_r12<LF>(a, MU, link_site, u);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      mc_load(up[k], hin + lidx<NRHS>(a.lay, ncb, k, r0));
+      mc_load(dn[k], hin + lidx<NRHS>(a.lay, ncb, 6 + k, r0));
+    }
+    // the time links of the last time slice carry the boundary factor
+    const bool edge = MU == 0 && (DIR > 0 ? c.t == a.g.T - 1 : c.t == 0);
+    rebuild_third_row(u, edge ? a.time_bc : 1.f);
+  } else if constexpr (BATCH) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = ldg_batch(lp + (int64_t)e * a.g.V);
 #pragma unroll
@@ -308,12 +355,12 @@ template <int K> struct DirOf {
   static constexpr int DIR = (K % 2 == 0) ? +1 : -1;
 };
 
-template <typename Real, int NR, bool BATCH, typename HIN, int NRHS, int PF, int K>
+template <typename Real, int NR, bool BATCH, typename HIN, int NRHS, int PF, int K, int LF = 0>
 __device__ __forceinline__ void hop_step(const DslashArgs<Real>& a, const Coord& c, int p, int r0, const HIN* hin,
                                          MC<Real, NR> acc[12]) {
   if constexpr (PF > 0 && K + PF < 8)
     prefetch_dir<Real, NR, DirOf<K + PF>::MU, DirOf<K + PF>::DIR, HIN, NRHS>(a, c, p, hin);
-  hop_dir<Real, NR, DirOf<K>::MU, DirOf<K>::DIR, BATCH, HIN, NRHS>(a, c, p, r0, hin, acc);
+  hop_dir<Real, NR, DirOf<K>::MU, DirOf<K>::DIR, BATCH, HIN, NRHS, LF>(a, c, p, r0, hin, acc);
 }
 
 // Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 strictly
@@ -379,7 +426,8 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
 }
 
 // The whole operator on one target site for this thread's NR rhs.
-template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0, int PF = 0>
+template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0, int PF = 0,
+          int LF = 0>
 __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site) {
   using C = typename Cplx<Real>::T;
   const int r0 = threadIdx.x * NR;
@@ -404,14 +452,14 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
       prefetch_dir<Real, NR, 0, +1, HIN, NRHS>(a, c, p, hin);
       if constexpr (PF > 1) prefetch_dir<Real, NR, 0, -1, HIN, NRHS>(a, c, p, hin);
     }
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 0>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 1>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 2>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 3>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 4>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 5>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 6>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 7>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 0, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 1, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 2, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 3, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 4, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 5, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 6, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 7, LF>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -461,12 +509,12 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
 }
 
 template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0, int PF = 0>
+          typename SIN, int NRHS = 0, int PF = 0, int LF = 0>
 __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   if (a.skip != nullptr && *a.skip != 0) return;
   if (!LOOP) {
     const int site = blockIdx.x * blockDim.y + threadIdx.y;
-    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF>(a, site);
+    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF>(a, site);
     return;
   }
   // persistent CTAs: each walks one contiguous chunk of target sites, blockDim.y
@@ -475,7 +523,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   const int s0 = blockIdx.x * a.loop_chunk;
   const int s1 = min(s0 + a.loop_chunk, a.n_target);
   for (int site = s0 + threadIdx.y; site < s1; site += blockDim.y)
-    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF>(a, site);
+    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF>(a, site);
 }
 
 // Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
@@ -491,6 +539,7 @@ struct DslashVariant {
   int prefetch = 0;    // with nrhs_fixed: L1 prefetch of the operands this many directions ahead
   int ring_warps = 0;  // > 0: the bulk-copy ring kernel (dslash_ring.cuh) with this many warps per CTA
   int ring_slots = 0;  //       and this many ring slots per warp
+  int links = 0;       // 1: reads the 12-real FP32 link copy (third row rebuilt)
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -503,9 +552,9 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
 template <typename Real, int NR, int SM, int PM, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0, int PF = 0>
+          typename SIN, int NRHS = 0, int PF = 0, int LF = 0>
 cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
-  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF>;
+  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF>;
   dim3 grid((a.n_target + block.y - 1) / block.y);
   if (PF > 0) {
     // the prefetched lines live in L1: ask for the smallest shared-memory carve-out
@@ -534,13 +583,16 @@ cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
 }
 
 template <typename Real, int NR, int MAXT, int MINB, bool BATCH, bool LOOP = false,
-          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0, int PF = 0>
+          typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0, int PF = 0,
+          int LF = 0>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
   if (NRHS > 0 && (a.lay.nrhs != NRHS || a.lay.log_s != 0)) return cudaErrorInvalidValue;
+  if (LF == 1 && a.links_r12 == nullptr) return cudaErrorInvalidValue;
+  if (LF == 2 && a.links_r12_bf16 == nullptr) return cudaErrorInvalidValue;
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
 #define LQCD_DS(SM, PM) \
-  return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF>(a, block, s)
+  return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF>(a, block, s)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -559,6 +611,11 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
 #define LQCD_DSLASH_VARIANT_NRHS_TU(REAL, NR, MAXT, MINB, NRHS, PF)                                        \
   template cudaError_t launch_dslash_variant<REAL, NR, MAXT, MINB, false, false, typename Cplx<REAL>::T, \
                                              typename Cplx<REAL>::T, NRHS, PF>(const DslashArgs<REAL>&, int, int, cudaStream_t);
+
+// ... and of an FP32 variant reading two-row links (LF = 1: FP32 rows, 2: BF16 rows).
+#define LQCD_DSLASH_VARIANT_LF_TU(NR, MAXT, MINB, LOOP, NRHS, PF, LF)                                      \
+  template cudaError_t launch_dslash_variant<float, NR, MAXT, MINB, false, LOOP, float2, float2, NRHS, PF, LF>( \
+      const DslashArgs<float>&, int, int, cudaStream_t);
 
 // FP32 arithmetic on BF16-stored inputs (hop input HIN, self-term input SIN), FP32 output.
 cudaError_t launch_dslash_bf16(const DslashArgs<float>& a, int self_mode, int post_mode, bool hop_bf16,

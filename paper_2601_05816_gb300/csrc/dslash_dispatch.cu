@@ -7,7 +7,7 @@ namespace lqcd {
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
 //  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance,
-//  ring kernel warps per CTA, ring slots per warp}
+//  ring kernel warps per CTA, ring slots per warp, two-row links}
 const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
                              {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16},
                              {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
@@ -20,7 +20,11 @@ const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 12
                              {2, 192, 2, 0, 0, 0, 16, 0, 6, 2}, {2, 512, 1, 0, 0, 0, 16, 0, 16, 1},
                              {2, 384, 1, 0, 0, 0, 32, 0, 12, 2}, {2, 224, 2, 0, 0, 0, 32, 0, 7, 2},
                              {2, 384, 1, 0, 0, 0, 64, 0, 12, 2}, {2, 224, 2, 0, 0, 0, 64, 0, 7, 2},
-                             {2, 256, 1, 0, 0, 0, 64, 0, 8, 3}};
+                             {2, 256, 1, 0, 0, 0, 64, 0, 8, 3},
+                             // two-row FP32 links (third row rebuilt)
+                             {1, 256, 1, 0, 0, 0, 0, 0, 0, 0, 1}, {2, 256, 2, 0, 0, 0, 0, 0, 0, 0, 1},
+                             {2, 128, 4, 0, 0, 0, 0, 0, 0, 0, 1}, {2, 256, 2, 0, 0, 1, 0, 0, 0, 0, 1},
+                             {2, 128, 4, 0, 0, 0, 16, 2, 0, 0, 1}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -50,6 +54,19 @@ LQCD_EXTERN_NRHS(128, 4, 32, 1)
 LQCD_EXTERN_NRHS(128, 4, 64, 0)
 LQCD_EXTERN_NRHS(128, 4, 64, 1)
 #undef LQCD_EXTERN_NRHS
+#define LQCD_EXTERN_LF(NR, MAXT, MINB, LOOP, NRHS, PF, LF)                                                  \
+  extern template cudaError_t launch_dslash_variant<float, NR, MAXT, MINB, false, LOOP, float2, float2, NRHS, PF, LF>( \
+      const DslashArgs<float>&, int, int, cudaStream_t);
+LQCD_EXTERN_LF(1, 256, 1, false, 0, 0, 1)
+LQCD_EXTERN_LF(2, 256, 2, false, 0, 0, 1)
+LQCD_EXTERN_LF(2, 128, 4, false, 0, 0, 1)
+LQCD_EXTERN_LF(2, 256, 2, true, 0, 0, 1)
+LQCD_EXTERN_LF(2, 128, 4, false, 16, 2, 1)
+LQCD_EXTERN_LF(1, 256, 1, false, 0, 0, 2)
+LQCD_EXTERN_LF(2, 128, 4, false, 0, 0, 2)
+LQCD_EXTERN_LF(2, 256, 2, true, 0, 0, 2)
+LQCD_EXTERN_LF(2, 128, 4, false, 16, 2, 2)
+#undef LQCD_EXTERN_LF
 extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
@@ -81,6 +98,18 @@ int dslash_default_variant(bool f64, int nrhs) {
 template <>
 cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int post_mode, int variant,
                                  cudaStream_t s) {
+  if (a.link_format == 2) {
+    // BF16 two-row links (a storage choice of the context, not a tuned variant): a fixed
+    // launch shape per rhs count
+    const int n = a.lay.nrhs;
+    if (n == 16 && a.lay.log_s == 0)
+      return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16, 2, 2>(a, self_mode, post_mode, s);
+    if (n % 2 == 0 && n / 2 <= 128) {
+      if (n <= 4) return launch_dslash_variant<float, 2, 256, 2, false, true, float2, float2, 0, 0, 2>(a, self_mode, post_mode, s);
+      return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 0, 0, 2>(a, self_mode, post_mode, s);
+    }
+    return launch_dslash_variant<float, 1, 256, 1, false, false, float2, float2, 0, 0, 2>(a, self_mode, post_mode, s);
+  }
   if (!dslash_variant_ok(false, variant, a.lay.nrhs)) variant = dslash_default_variant(false, a.lay.nrhs);
   const DslashVariant v = kF32[variant];
   if (v.ring_warps > 0) {
@@ -116,6 +145,11 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
     LQCD_CASE_NRHS(20, 128, 4, 64, 0)
     LQCD_CASE_NRHS(21, 128, 4, 64, 1)
 #undef LQCD_CASE_NRHS
+    case 33: return launch_dslash_variant<float, 1, 256, 1, false, false, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
+    case 34: return launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
+    case 35: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
+    case 36: return launch_dslash_variant<float, 2, 256, 2, false, true, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
+    case 37: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16, 2, 1>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -15,6 +15,8 @@ cudaError_t launch_spinor_layout(const Geom& g, int sites, int nrhs, int log_s, 
 // Site-major FP32 copies for the ring hopping kernel: links [4][V][10] float2, blocks [V][72] float.
 cudaError_t launch_links_aos(int V, const void* links32, void* aos, cudaStream_t s);
 cudaError_t launch_blocks_aos(int V, const void* blk32, void* aos, cudaStream_t s);
+// Rows 0 and 1 of the FP32 links: [4][6][V] float2 and the same rounded to BF16 pairs.
+cudaError_t launch_links_r12(int V, const void* links32, void* r12, void* r12_bf16, cudaStream_t s);
 // Column map of the solver's compaction (at most 64 rhs).
 struct ColumnMap {
   int col[64];

@@ -523,7 +523,15 @@ struct Profile {
 static double op_algorithmic_bytes(const lqcd_ctx_s* ctx, int op, bool f64, int nrhs, bool bf16 = false) {
   const double s = f64 ? 8.0 : 4.0;
   const bool clover = ctx->c_sw != 0.0;
-  const double fixed = op == LQCD_OP_FULL ? (clover ? 144.0 : 72.0) : (clover ? 432.0 : 288.0);
+  // links: 72 reals per site (full) or 288 per odd site (Schur) in the 18-real form; the
+  // two-row forms read 12 reals per link (BF16 storage: 2 bytes each, expressed in units of s)
+  double link_reals = op == LQCD_OP_FULL ? 72.0 : 288.0;
+  if (!f64) {
+    const int v = tuned_variant(ctx, false, nrhs, op);
+    if (ctx->link_format == LQCD_LINKS_BF16) link_reals *= (12.0 * 2.0) / (18.0 * 4.0);
+    else if (v >= 0 && dslash_variant(false, v).links == 1) link_reals *= 12.0 / 18.0;
+  }
+  const double fixed = (op == LQCD_OP_FULL ? (clover ? 72.0 : 0.0) : (clover ? 144.0 : 0.0)) + link_reals;
   if (bf16) {  // BF16 input read (2 bytes per real), FP32 intermediate and output
     if (op == LQCD_OP_FULL) return (double)ctx->g.V * (24.0 * nrhs * 2 + 24.0 * nrhs * 4 + fixed * 4);
     return (double)ctx->g.Vh * (2 * 24.0 * nrhs * 2 + 3 * 24.0 * nrhs * 4 + fixed * 4);

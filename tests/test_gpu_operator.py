@@ -469,3 +469,71 @@ def test_orthogonalise_bf16_basis(nvec, nrhs):
     torch.cuda.synchronize()
     assert np.max(np.abs(h.cpu().numpy() - (h1 + h2))) < 2e-5 * np.max(np.abs(h1))
     assert relerr(wout.cpu().numpy().reshape(nrhs, N), w2) < 1e-5
+
+
+def _bf16_link_rows(U):
+    """The links the BF16 two-row storage represents: rows 0 and 1 of every U_mu(x) rounded to
+    BF16 (through FP32, as the library rounds its FP32 copy), row 2 rebuilt as conj(row0 x row1)
+    in FP64 (an SU(3) matrix's third row)."""
+    Ur = _bf16_round(U)
+    Ur[..., 2, :] = np.conj(np.cross(Ur[..., 0, :], Ur[..., 1, :]))
+    return Ur
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+@pytest.mark.parametrize("op", [lq.OP_FULL, lq.OP_SCHUR])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 16])
+def test_bf16_link_storage_operator(case, op, nrhs):
+    """The FP32 operator with BF16 two-row link storage equals the oracle's operator on the links it
+    represents (hopping term on the rounded links, clover blocks from the exact ones), to the FP32
+    tolerance; and it differs from the FP32-link operator (the rounding is real)."""
+    dims, kind, eps, m0, c_sw = case
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    Ur = _bf16_link_rows(U)
+    psi = syn.gaussian_spinors(dims, nrhs, 800 + nrhs)
+    src = psi if op == lq.OP_FULL else oracle.split_parity(psi, 1)
+    ref = (oracle.apply_D(Ur, src, m0, C if c_sw else None) if op == lq.OP_FULL
+           else oracle.apply_schur(Ur, A, Ainv, src))
+    exact = (oracle.apply_D(U, src, m0, C if c_sw else None) if op == lq.OP_FULL
+             else oracle.apply_schur(U, A, Ainv, src))
+    d_in = dev(src, lq.C64)
+    d_out = torch.empty_like(d_in)
+    lat.set_link_storage(lq.LINKS_BF16)
+    try:
+        assert lat.link_storage() == lq.LINKS_BF16
+        lat.apply(op, nrhs, d_in, d_out)
+        torch.cuda.synchronize()
+    finally:
+        lat.set_link_storage(lq.LINKS_FP32)
+    got = d_out.cpu().numpy()
+    assert relerr(got, ref) < TOL[lq.C64]
+    assert relerr(got, exact) > 1e-4
+
+
+@pytest.mark.parametrize("nrhs", [4, 16])
+def test_bf16_spinors_and_links_operator(nrhs):
+    """BF16-stored input and BF16 two-row links together (the operator of the BF16-basis solve with
+    BF16 links): the oracle on the rounded input and the rounded links."""
+    dims, kind, eps, m0, c_sw = CASES[0]
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    Ur = _bf16_link_rows(U)
+    psi_o = oracle.split_parity(syn.gaussian_spinors(dims, nrhs, 900 + nrhs), 1)
+    ref = oracle.apply_schur(Ur, A, Ainv, _bf16_round(psi_o))
+    d_in = torch.from_numpy(np.ascontiguousarray(psi_o)).to(torch.complex64).cuda()
+    d_out = torch.empty_like(d_in)
+    lat.set_link_storage(lq.LINKS_BF16)
+    try:
+        lat.apply(lq.OP_SCHUR, nrhs, d_in, d_out, dtype=lq.BF16S)
+        torch.cuda.synchronize()
+    finally:
+        lat.set_link_storage(lq.LINKS_FP32)
+    assert relerr(d_out.cpu().numpy(), ref) < TOL[lq.C64]
+
+
+def test_two_row_variants_read_fewer_link_bytes():
+    """The autotuner's two-row FP32 link variants report 12 reals per link, the others 18."""
+    lat, *_ = setup(*CASES[0][:5], 101)
+    lib = lq.load()
+    reals = [lat.variant_link_reals(lq.C64, v) for v in range(lib.lqcd_kernel_variant_count(lq.C64))]
+    assert set(reals) == {12, 18} and reals.count(12) >= 4
+    assert all(lat.variant_link_reals(lq.C128, v) == 18 for v in range(lib.lqcd_kernel_variant_count(lq.C128)))

@@ -391,3 +391,25 @@ def test_retirement_compacts_the_active_rhs(precision, op):
     for k in range(nrhs):
         assert np.linalg.norm(xc[k] - xn[k]) <= 1e-6 * np.linalg.norm(xn[k]), k
     lat.close()
+
+
+@pytest.mark.parametrize("precision", [lq.C64, lq.BF16S])
+def test_mixed_solve_with_bf16_links(precision):
+    """The FP32 inner operator on BF16 two-row links (an O(2^-9) perturbation of D): the FP64
+    refinement on the exact links still brings every rhs to 1e-10 with the oracle's operator."""
+    dims = (8, 8, 8, 8)
+    m0, c_sw = -0.2, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1001)
+    b = syn.gaussian_spinors(dims, 4, 1401)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    lat.set_link_storage(lq.LINKS_BF16)
+    x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    res = lat.solve(torch.from_numpy(b).cuda(), x, 4, op=lq.OP_SCHUR, precision=precision, restart_len=32,
+                    tol=1e-10, max_restarts=400)
+    torch.cuda.synchronize()
+    assert res.status == lq.OK, res
+    rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
+    assert np.all(rel <= 1e-10), rel
+    lat.close()
