@@ -684,12 +684,15 @@ def run_gpu(args, w):
     if rank == 0 and not args.skip_extras:
         extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line)
         extras_gmres(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, inner, results, line)
+        if nrhs <= 16:
+            extras_block(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, line)
         extras_e2e(args, w, lat, lq, torch, U, b, nrhs, solve_kw, line)
         extras_oracle_check(args, w, lq, torch, U, b, x_d, lat, nrhs, solve_kw, line)
     lat.close()
     del U_d, b_d, x_d
     torch.cuda.empty_cache()
     if rank == 0 and not args.skip_extras:
+        extras_batch(args, lq, torch, line)
         if not args.skip_large:
             extras_gmres_large(args, lq, torch, line)
         # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
@@ -777,6 +780,25 @@ def extras_gmres(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, inner, resul
                              "no graph replay; mixed_graph_s is the same solve replayed as CUDA graphs)"}
 
 
+def extras_block(args, w, lat, lq, torch, b_d, x_d, nrhs, solve_kw, line):
+    """Block GMRES (one Krylov space for the 16 rhs, FP32 block cycles in FP64 refinement) against the
+    batched solver on the same problem: time to solution, Arnoldi steps, true residual."""
+    lat.set_clover(w["m0"], w["c_sw"])
+    out = {}
+    for name, kw in (("batched", dict(solve_kw, profile=False)),
+                     ("block", dict(solve_kw, profile=False, block=True, use_graph=False))):
+        x_d.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lat.solve(b_d, x_d, nrhs, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "status": r.status, "iterations": r.iterations,
+                     "fp64_residuals": r.outer_steps, "cycles": r.restarts, "relres_max": r.relres_max}
+    out["note"] = ("iterations = Arnoldi steps per rhs; one block step applies the operator to all rhs at once "
+                   "and orthogonalises against every rhs's basis vectors")
+    line["block_gmres"] = out
+
+
 def extras_e2e(args, w, lat, lq, torch, U, b, nrhs, solve_kw, line):
     """End to end through the C ABI with pinned host buffers (copies inside the timed region)."""
     U_h = torch.from_numpy(U).pin_memory()
@@ -848,6 +870,57 @@ def extras_oracle_check(args, w, lq, torch, U, b, x_d, lat, nrhs, solve_kw, line
                            "note": "the oracle's FP64 operator applied to the GPU's mixed-precision solution"},
         "solution_error_4x4x4x4": {"config": "4^4 Haar Wilson m0 0.1, 2 rhs, GMRES(30) to 1e-10; oracle "
                                              "solution to 1e-13", "solves": small}}
+
+
+def extras_batch(args, lq, torch, line):
+    """The uneven multi-lattice batch (8^4 / 12^4 / 16^4 / 16^3x32 with 4 / 8 / 16 / 32 rhs, one
+    lqcd_solve_batch: one captured graph per restart round, a branch per lattice) against the same
+    four solves one after another; each the mean of three runs after one warm-up."""
+    import synthetic as syn
+    wb = WORKLOADS["batch"]
+    lats, bs, xs, nr = [], [], [], []
+    units = 0
+    for k, (dims, eps, m0, nrhs) in enumerate(wb["lattices"]):
+        U = torch.from_numpy(syn.gauge_field(dims, "exp", eps, seed=wb["gauge_seed"] + k)).cuda()
+        b = torch.from_numpy(syn.gaussian_spinors(dims, nrhs, wb["rhs_seed"] + k)).cuda()
+        lat = lq.Lattice(dims, time_bc=-1)
+        lat.set_gauge(U)
+        lat.set_clover(m0, wb["c_sw"])
+        lat.tune(lq.C64, nrhs, reps=3)
+        lats.append(lat); bs.append(b); xs.append(torch.zeros_like(b)); nr.append(nrhs)
+        units += dims[0] * dims[1] * dims[2] * dims[3] * nrhs
+    kw = dict(op=lq.OP_SCHUR, precision=lq.C64, restart_len=wb["restart"], tol=wb["tol"],
+              max_restarts=args.max_restarts)
+
+    def batch():
+        for x in xs:
+            x.zero_()
+        return lq.solve_batch(lats, bs, xs, nr, **kw)
+
+    def sequential():
+        out = []
+        for lat, b, x, n in zip(lats, bs, xs, nr):
+            x.zero_()
+            out.append(lat.solve(b, x, n, **kw))
+        return out
+
+    res = {}
+    for name, fn in (("batch", batch), ("sequential", sequential)):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            r = fn()
+        torch.cuda.synchronize()
+        res[name] = ((time.perf_counter() - t0) / 3, r)
+    tb, rb = res["batch"]
+    ts, rs_ = res["sequential"]
+    line["batch"] = {"workload": wb["name"], "batch_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+                     "site_rhs_per_s": units / tb, "iterations": [r.iterations for r in rb],
+                     "relres_max": [r.relres_max for r in rb],
+                     "status": [r.status for r in rb] + [r.status for r in rs_]}
+    for lat in lats:
+        lat.close()
 
 
 def extras_gmres_large(args, lq, torch, line):

@@ -252,6 +252,14 @@ typedef struct {
                          pass through the operator and Gram-Schmidt kernels; the FP64 residual
                          of the new block is recomputed once. 0: retired rhs stay in the block
                          and only stop contributing basis vectors */
+  int block;          /* 1: block GMRES (Sec. II's block Krylov solvers; not the paper's
+                         method) as the inner solver: every FP64 residual r is followed by
+                         one block GMRES(m) cycle on D e = r in FP32 over one Krylov space
+                         shared by all rhs (block CGS2 with Cholesky-QR, Householder least
+                         squares), ending when every rhs's residual estimate is below
+                         max(tol ||b|| / 2, inner_tol ||r||); converged rhs always leave the
+                         block. Needs precision LQCD_C64 and nrhs <= 16; reorth and use_graph
+                         are ignored; the stream is synchronised after every step */
 } lqcd_solve_params;
 
 typedef struct {

@@ -38,6 +38,7 @@ class SolveParams(ctypes.Structure):
         ("max_restarts", ctypes.c_int), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
         ("x0_given", ctypes.c_int), ("use_graph", ctypes.c_int), ("reorth", ctypes.c_int),
         ("profile", ctypes.c_int), ("dagger", ctypes.c_int), ("compact", ctypes.c_int),
+        ("block", ctypes.c_int),
     ]
 
 
@@ -300,11 +301,12 @@ class Lattice:
     def solve(self, b, x, nrhs: int, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,
               max_restarts: int = 200, tol: float = 1e-10, inner_tol: float = 0.0, x0_given: bool = False,
               use_graph: bool = True, reorth: int = 2, profile: bool = False, dagger: bool = False,
-              compact: bool = True, stream=None) -> SolveResult:
+              compact: bool = True, block: bool = False, stream=None) -> SolveResult:
         """Batched GMRES on D x = b (dagger: D^dagger x = b); b and x complex128 canonical [nrhs][V][4][3],
         host (numpy) or device."""
         p = SolveParams(op, precision, restart_len, max_restarts, tol, inner_tol, int(x0_given), int(use_graph),
-                        int(reorth), int(profile), int(dagger), int(compact))  # reorth: 0 CGS1, 1 CGS2, 2 delayed CGS2
+                        int(reorth), int(profile), int(dagger), int(compact), int(block))
+        # reorth: 0 CGS1, 1 CGS2, 2 delayed CGS2; block: block GMRES inner solver
         its = (ctypes.c_int * nrhs)()
         rel = (ctypes.c_double * nrhs)()
         st = SolveStats()
@@ -336,7 +338,7 @@ def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = 
     tols = list(tol) if isinstance(tol, (list, tuple)) else [tol] * n
     ctxs = (ctypes.c_void_p * n)(*[lat.handle.value for lat in lattices])
     params = (SolveParams * n)(*[SolveParams(op, precision, restart_len, max_restarts, tols[i], inner_tol, 0,
-                                             int(use_graph), int(reorth), 0, 0, int(compact)) for i in range(n)])
+                                             int(use_graph), int(reorth), 0, 0, int(compact), 0) for i in range(n)])
     nr = (ctypes.c_int * n)(*[int(v) for v in nrhs])
     bp = (ctypes.c_void_p * n)(*[_ptr(v) for v in bs])
     xp = (ctypes.c_void_p * n)(*[_ptr(v) for v in xs])

@@ -719,17 +719,19 @@ update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstrid
   const int r = threadIdx.x % nrhs;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    Real sr = 0, si = 0;
+    // eight basis loads in flight per thread (independent partial sums), not a chain of k
+    Real sr[2] = {0, 0}, si[2] = {0, 0};
+#pragma unroll 8
     for (int i = 0; i < k; ++i) {
       const double2 c = ys[i * nrhs + r];
       const C v = C(ld_basis(basis + i * vstride + e));
       const Real crr = (Real)c.x, cii = (Real)c.y;
-      sr += crr * v.x - cii * v.y;
-      si += crr * v.y + cii * v.x;
+      sr[i & 1] += crr * v.x - cii * v.y;
+      si[i & 1] += crr * v.y + cii * v.x;
     }
     double2 xv = x[e];
-    xv.x += (double)sr;
-    xv.y += (double)si;
+    xv.x += (double)(sr[0] + sr[1]);
+    xv.y += (double)(si[0] + si[1]);
     x[e] = xv;
   }
 }

@@ -82,6 +82,10 @@ lqcd_status apply_operator(lqcd_ctx ctx, int op, bool f64, int nrhs, const void*
                            void* tmp, const int* skip, cudaStream_t stream);
 lqcd_status apply_operator_bf16in(lqcd_ctx ctx, int op, int nrhs, const void* in, void* out, void* tmp,
                                   const int* skip, cudaStream_t stream);
+// One block GMRES(m) cycle (block_gmres.cu) on D e = r for nrhs <= 16 rhs: x (FP64) += e.
+lqcd_status block_gmres_cycle(lqcd_ctx ctx, int op, int nrhs, int m, int64_t n_sys, void* basis, void* tmp_even,
+                              const void* r64, void* x64, const double* thr, double* h_res, int* h_flag, int* steps,
+                              cudaStream_t st);
 lqcd_status schur_prepare(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, void* bhat_o,
                           void* tmp_even, cudaStream_t stream);
 lqcd_status schur_reconstruct(lqcd_ctx ctx, bool f64, int nrhs, const void* b_full, const void* x_o,

@@ -651,6 +651,8 @@ struct Staging {
   int active[256];
   int kcycle[256];
   int wait_err;             // the streaming kernels' pipeline-wait flag
+  double block_res[64];     // block GMRES: residual norm per rhs after the last step
+  int block_flag;           // block GMRES: rank-deficient block met
 };
 
 // One lattice's batched-GMRES solve, split into the phases of a restart so that
@@ -741,6 +743,8 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
       (P.dagger != 0 && P.dagger != 1))
     return set_error(LQCD_ERR_ARG,
                      "lqcd_solve: bad parameters (nrhs 1..64, 1..32 for BF16 storage, restart_len 1..64, tol > 0)");
+  if (P.block && (P.precision != LQCD_C64 || nrhs > 16))
+    return set_error(LQCD_ERR_ARG, "lqcd_solve: block GMRES needs precision LQCD_C64 and at most 16 rhs");
   eo = P.op == LQCD_OP_SCHUR;
   f64_inner = P.precision == LQCD_C128;
   bf16 = P.precision == LQCD_BF16S;
@@ -784,7 +788,7 @@ lqcd_status SolveJob::setup(lqcd_ctx c, const lqcd_solve_params* params, int nr,
     else if ((st = workspace(ctx, "schur_tmp32", (size_t)n_half * sizeof(float2), &B.tmp_even_in)) != LQCD_OK)
       return st;
   }
-  nested = !f64_inner;
+  nested = !f64_inner && !P.block;   // block GMRES: one block cycle per FP64 residual
   if (nested) {
     if ((st = workspace(ctx, "solve_x_outer", (size_t)n_sys * sizeof(double2), &x_outer)) != LQCD_OK) return st;
     if ((st = workspace(ctx, "solve_r_outer", (size_t)n_sys * sizeof(double2), &r_outer)) != LQCD_OK) return st;
@@ -1036,7 +1040,9 @@ lqcd_status SolveJob::decide(bool* run) {
       finished = true;
       return LQCD_OK;
     }
-    if (P.compact && nrhs - n_active >= std::max(1, nrhs / 8)) {
+    // (block GMRES always removes converged rhs: their near-zero residual columns would make
+    // the block's Gram matrix ill-conditioned)
+    if ((P.compact || P.block) && nrhs - n_active >= (P.block ? 1 : std::max(1, nrhs / 8))) {
       // retire the converged rhs from the block: the solve continues on the active
       // columns only, so the operator and Gram-Schmidt move fewer bytes; the FP64
       // residual of the compacted block is computed next
@@ -1083,6 +1089,19 @@ lqcd_status SolveJob::decide(bool* run) {
 // One restart cycle on stream cs: v_0, m Arnoldi steps, back substitution, x += V y.
 lqcd_status SolveJob::enqueue_cycle(cudaStream_t cs, bool allow_graph) {
   lqcd_status st;
+  if (P.block) {
+    int steps = 0;
+    if ((st = block_gmres_cycle(ctx, P.op, nrhs, m, n_sys, B.basis, B.tmp_even_in, r64, sys_x, hs->thr,
+                                hs->block_res, &hs->block_flag, &steps, cs)) != LQCD_OK)
+      return st;
+    for (int r = 0; r < nrhs; ++r)
+      if (active_outer[r]) iters[r] += steps;
+    // per step: operator, 2 x (Gram + reduction + update), 2 x (Gram + reduction + Cholesky + scale),
+    // least-squares step; per cycle: v0, 2 x CholQR, ls init, solve, x update
+    nl += (long long)steps * ((eo ? 2 : 1) + 6 + 8 + 1) + 1 + 8 + 1 + 2;
+    ++restarts;
+    return LQCD_OK;
+  }
   LQCD_CUDA(launch_cycle_init(B.st, d_beta0, cs), "cycle init");
   LQCD_CUDA(launch_scale_convert(f64_inner, n_sys, nrhs, r64, B.st.scale, B.basis, cs, bf16), "v0");
   if (allow_graph) {
@@ -1236,6 +1255,9 @@ lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_pa
   for (int i = 0; i < nlat; ++i)
     for (int k = 0; k < i; ++k)
       if (ctxs[i] == ctxs[k]) return set_error(LQCD_ERR_ARG, "lqcd_solve_batch: lattice %d appears twice", i);
+  for (int i = 0; i < nlat; ++i)
+    if (params[i].block)
+      return set_error(LQCD_ERR_ARG, "lqcd_solve_batch: block GMRES (params.block) is available in lqcd_solve only");
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<SolveJob> jobs(nlat);
   lqcd_status st;

@@ -413,3 +413,48 @@ def test_mixed_solve_with_bf16_links(precision):
     rel = oracle_relres(U, m0, c_sw, b, x.cpu().numpy())
     assert np.all(rel <= 1e-10), rel
     lat.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 6, 16])
+@pytest.mark.parametrize("op", [lq.OP_SCHUR, lq.OP_FULL])
+def test_block_gmres_solve(nrhs, op):
+    """Block GMRES (one Krylov space shared by all rhs, FP32 inner cycles in FP64 refinement): every rhs
+    meets 1e-10 with the oracle's operator, the solution agrees with the batched solver's, and the block
+    space of dimension m * nrhs needs no more Arnoldi steps per rhs than the independent spaces."""
+    dims = (8, 8, 8, 8)
+    m0, c_sw = -0.2, 1.0
+    U = syn.gauge_field(dims, "exp", 0.3, seed=1001)
+    b = syn.gaussian_spinors(dims, nrhs, 1501 + nrhs)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(torch.from_numpy(U).cuda())
+    lat.set_clover(m0, c_sw)
+    xb = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    rb = lat.solve(torch.from_numpy(b).cuda(), xb, nrhs, op=op, precision=lq.C64, restart_len=32, tol=1e-10,
+                   block=True, max_restarts=400)
+    xn = torch.zeros_like(xb)
+    rn = lat.solve(torch.from_numpy(b).cuda(), xn, nrhs, op=op, precision=lq.C64, restart_len=32, tol=1e-10,
+                   max_restarts=400)
+    torch.cuda.synchronize()
+    assert rb.status == lq.OK and rn.status == lq.OK, (rb, rn)
+    xs = xb.cpu().numpy()
+    rel = oracle_relres(U, m0, c_sw, b, xs)
+    assert np.all(rel <= 1e-10), rel
+    assert np.allclose(rel, rb.relres_per_rhs, rtol=1e-3, atol=1e-13)
+    xr = xn.cpu().numpy()
+    for k in range(nrhs):
+        assert np.linalg.norm(xs[k] - xr[k]) <= 1e-6 * np.linalg.norm(xr[k]), k
+    assert rb.iterations <= rn.iterations + 8, (rb.iterations, rn.iterations)
+    lat.close()
+
+
+def test_block_gmres_argument_checks():
+    dims = (4, 4, 4, 4)
+    lat = lq.Lattice(dims)
+    lat.set_gauge(syn.gauge_field(dims, "exp", 0.3, seed=3))
+    lat.set_clover(0.1, 1.0)
+    b = syn.gaussian_spinors(dims, 17, 4)
+    with pytest.raises(lq.LqcdError):   # at most 16 rhs per block
+        lat.solve(b, np.zeros_like(b), 17, precision=lq.C64, block=True)
+    with pytest.raises(lq.LqcdError):   # FP32 inner cycles only
+        lat.solve(b[:2], np.zeros_like(b[:2]), 2, precision=lq.C128, block=True)
+    lat.close()
