@@ -711,6 +711,8 @@ def extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     lat.set_gauge(U_d)
     lat.set_clover(w["m0"], w["c_sw"])
+    # measured SIMT FMA rates: the FP64 applies are bound by them, not by HBM
+    alu_peak = {"c64": lq.fma_peak(False), "c128": lq.fma_peak(True)}
     sweep = []
     nr_list = [int(v) for v in args.sweep.split(",")] if args.sweep else [1, 2, 4, 8, 16, 32, 64]
     for nr in nr_list:
@@ -718,10 +720,15 @@ def extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line):
             lat.tune(dt, nr, reps=3)
             for op in (lq.OP_SCHUR, lq.OP_FULL):
                 tt, nb, units, lb = dslash_point(lat, lq, torch, dims, nr, dt, op, args.dslash_reps, flush)
-                sweep.append({"nrhs": nr, "dtype": "c64" if dt == lq.C64 else "c128",
+                dname = "c64" if dt == lq.C64 else "c128"
+                # flops: ~1870 per site and rhs for the full operator (8 x 168 hopping, 504 clover block,
+                # scaling and the self term), twice that per odd site and rhs for the Schur complement
+                tfl = units * (1870.0 if op == lq.OP_FULL else 3740.0) / tt / 1e12
+                sweep.append({"nrhs": nr, "dtype": dname,
                               "op": "schur" if op == lq.OP_SCHUR else "full", "ms": tt * 1e3,
                               "variant": lat.kernel_variant(dt, nr, op), "link_bytes": lb,
                               "GB_s": nb / tt / 1e9, "frac_hbm": nb / tt / 1e9 / peak,
+                              "tflops": tfl, "frac_alu": tfl / alu_peak[dname],
                               "site_rhs_per_s": units / tt})
     # BF16 two-row link storage (the FP32 operator with links rounded to BF16) at small rhs counts,
     # where the links are the largest share of the bytes
@@ -740,7 +747,9 @@ def extras_sweep(args, w, lat, lq, torch, dims, U_d, peak, line):
     line["dslash"] = {"lattice": line["config"]["lattice"], "bytes_model": "full (48 b s + 4 L + 72 s) per site, "
                       "schur (120 b s + 16 L + 144 s) per odd site; L = bytes per link read (18 or 12 reals)",
                       "l2_flush": "512 MB memset between applies",
-                      "applies_per_point": args.dslash_reps, "statistic": "median", "points": sweep,
+                      "applies_per_point": args.dslash_reps, "statistic": "median",
+                      "alu_peak_tflops": alu_peak, "alu_peak_kind": "measured (lqcd_fma_peak: SIMT FMA chains)",
+                      "points": sweep,
                       "bf16_two_row_links": bf16_links}
 
 

@@ -350,6 +350,12 @@ lqcd_status lqcd_solve_batch(int nlat, const lqcd_ctx* ctxs, const lqcd_solve_pa
  * set_clover (which allocate, at set-up). */
 lqcd_status lqcd_apply_schur_noalloc(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs,
                                      const void* in, void* out, void* stream);
+/* Measured SIMT FMA rate of the current GPU (not in the paper; a roofline denominator for
+ * the FP64 kernels, which are bound by it): *tflops receives the best of three timed launches
+ * of independent FMA chains, in TFLOP/s (2 flops per FMA), FP64 if f64 != 0 else FP32.
+ * Allocates a small scratch buffer; synchronises `stream`. */
+lqcd_status lqcd_fma_peak(int f64, double* tflops, void* stream);
+
 /* Size in bytes of the fixed scratch array used by lqcd_apply_schur_noalloc. */
 size_t lqcd_noalloc_scratch_bytes(void);
 

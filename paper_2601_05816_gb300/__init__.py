@@ -82,6 +82,7 @@ _SIGS = {
     "lqcd_get_kernel_variant": (_I, [_VP, _I, _I, _I]),
     "lqcd_set_kernel_variant": (_I, [_VP, _I, _I, _I, _I]),
     "lqcd_set_link_storage": (_I, [_VP, _I]),
+    "lqcd_fma_peak": (_I, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     "lqcd_kernel_variant_link_reals": (_I, [_I, _I]),
     "lqcd_get_link_storage": (_I, [_VP]),
 }
@@ -324,6 +325,13 @@ class Lattice:
         x, lam [nrhs][V][4][3] and grad_U [V][4][3][3] (overwritten)."""
         _check(self._lib.lqcd_force(self._h, int(nrhs), _ptr(x), _ptr(lam), _ptr(grad_U), _stream(stream)),
                "lqcd_force")
+
+
+def fma_peak(f64: bool, stream=None) -> float:
+    """Measured SIMT FMA rate of the current GPU in TFLOP/s (lqcd_fma_peak): FP64 or FP32."""
+    v = ctypes.c_double(0.0)
+    _check(load().lqcd_fma_peak(int(bool(f64)), ctypes.byref(v), _stream(stream)), "lqcd_fma_peak")
+    return float(v.value)
 
 
 def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,

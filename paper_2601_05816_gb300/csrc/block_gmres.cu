@@ -20,6 +20,7 @@
 // inverses, the Householder step). The host reads the p residual norms after each step.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ctx.h"
@@ -383,9 +384,17 @@ struct BlockGmres {
     const int64_t rows_per_cta = 256 / gs;
     int64_t ctas = (rows + rows_per_cta - 1) / rows_per_cta;
     if (ctas > (int64_t)ctx->num_sms * 8) ctas = (int64_t)ctx->num_sms * 8;
+    // coefficients of up to 65 blocks of 16 x 16: beyond the default 48 KB of dynamic shared memory
 #define LQCD_RM(G)                                                                                              \
-  blk::rowmul_kernel<G, MODE><<<(int)ctas, 256, smem, st>>>(rows, p, nblk, (const float2*)V, n_sys, C, (float2*)W, \
-                                                            (double2*)X)
+  {                                                                                                             \
+    static std::once_flag attr;                                                                                 \
+    std::call_once(attr, [] {                                                                                   \
+      cudaFuncSetAttribute(blk::rowmul_kernel<G, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                           (int)(sizeof(float2) * 65 * blk::kMaxP * blk::kMaxP));                               \
+    });                                                                                                         \
+    blk::rowmul_kernel<G, MODE><<<(int)ctas, 256, smem, st>>>(rows, p, nblk, (const float2*)V, n_sys, C,        \
+                                                              (float2*)W, (double2*)X);                         \
+  }
     switch (gs) {
       case 1: LQCD_RM(1); break;
       case 2: LQCD_RM(2); break;
