@@ -672,7 +672,9 @@ def run_gpu(args, w):
                        "gram_schmidt": {0: "CGS1", 1: "CGS2", 2: "delayed CGS2"}.get(results[0].ortho, "?"),
                        "parallelism": f"rhs batches, {world} independent rank(s)",
                        "l2": "working set (basis 33 x %.0f MB) far above the 129 MB L2" %
-                             ((V // 2) * 12 * nrhs * 8 / 1e6)},
+                             ((V // 2) * 12 * nrhs * 8 / 1e6),
+                       "timed_path": "profiled solves: CUDA events around every operator and Gram-Schmidt "
+                                     "launch, so no graph replay (the graph-replayed solve is gmres.mixed_graph_s)"},
             "roofline": roofline, "clocks": clocks,
             "solve": {"iterations": [r.iterations for r in results], "restarts": [r.restarts for r in results],
                       "fp64_residuals": [r.outer_steps for r in results],

@@ -168,7 +168,7 @@ struct Small {
 };
 
 // Cholesky G = R^H R (upper R) and R^{-1}, one thread (p <= 16); mode 0: Racc = R,
-// mode 1: Racc = R Racc. flag is set when a pivot is <= 1e-28 * max diag (rank deficiency).
+// mode 1: Racc = R Racc. flag is set when a pivot is <= 1e-10 * max diag (rank deficiency).
 __global__ void chol_kernel(Small s, int mode) {
   if (threadIdx.x != 0) return;
   const int p = s.p;
@@ -180,9 +180,12 @@ __global__ void chol_kernel(Small s, int mode) {
     // R[j][j] = sqrt(G[j][j] - sum_k |R[k][j]|^2); R[j][c] = (G[j][c] - sum_k conj(R[k][j]) R[k][c]) / R[j][j]
     double d = s.G[j * p + j].x;
     for (int k = 0; k < j; ++k) d -= R[k * p + j].x * R[k * p + j].x + R[k * p + j].y * R[k * p + j].y;
-    if (!(d > 1e-28 * dmax)) {
+    // a pivot below 1e-10 of the largest diagonal entry: the block's columns are dependent to
+    // within FP32 rounding (singular values below 1e-5 of the largest); its normalisation would
+    // only amplify rounding noise
+    if (!(d > 1e-10 * dmax)) {
       *s.flag = 1;
-      d = fmax(d, 1e-28 * dmax + 1e-300);
+      d = fmax(d, 1e-10 * dmax + 1e-300);
     }
     const double rjj = sqrt(d);
     R[j * p + j] = make_double2(rjj, 0.0);
@@ -494,13 +497,16 @@ lqcd_status block_gmres_cycle(lqcd_ctx ctx, int op, int nrhs, int m, int64_t n_s
     LQCD_CUDA(cudaMemcpyAsync(h_res, bg.s.res, sizeof(double) * p, cudaMemcpyDeviceToHost, st), "read res");
     LQCD_CUDA(cudaMemcpyAsync(h_flag, bg.s.flag, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
     LQCD_CUDA(cudaStreamSynchronize(st), "block step sync");
-    k = j + 1;
-    bool done = true;
+    bool finite = true, done = true;
     for (int c = 0; c < p; ++c) {
-      if (!std::isfinite(h_res[c])) return set_error(LQCD_ERR_NONFINITE, "block GMRES: non-finite residual");
+      finite = finite && std::isfinite(h_res[c]);
       done = done && h_res[c] <= thr[c];
     }
-    // a rank-deficient new block (happy breakdown of the block Krylov space): stop here
+    // A non-finite estimate: step j is discarded (its reflectors act on rows >= j p only, so the
+    // least squares of steps 0..j-1 stand). A rank-deficient new block (the block form of a happy
+    // breakdown, or FP32 rounding in a nearly dependent block): step j is kept, the cycle ends.
+    if (!finite) break;
+    k = j + 1;
     if (done || *h_flag) break;
   }
   blk::ls_solve_kernel<<<1, 32, 0, st>>>(bg.s, k);
