@@ -68,13 +68,13 @@ WORKLOADS = {
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and algorithmic bytes of the
-# streaming Gram-Schmidt launches of one full 32-step Arnoldi cycle (64 launches, 1 .. 32
-# basis vectors) of the default workload, from one ncu capture each, keyed by (workload,
-# precision, Gram-Schmidt variant); the summaries are under profiles/. The reported traffic
-# per step is the timed solve's algorithmic bytes per step times their ratio (the timed
-# steps have a different mix of basis sizes than one full cycle). Cases not captured: null.
-GS_DRAM_CAPTURE = {("solve", "c64", 2): (115.670896896e9, 1152 * 100663296.0),
-                   ("solve", "bf16", 2): (60.98132736e9, 1216 * 50331648.0)}
+# streaming Gram-Schmidt kernel from one small single-kernel ncu capture (`--workload ortho
+# --nvec 32`: the three passes of one 32-vector CGS2 step on the 16^3 x 32 odd sites, 16 rhs;
+# the summary is under profiles/). The solve's passes are the same kernel with other flags, so
+# the reported traffic per step is the timed solve's algorithmic bytes per step times this
+# ratio (FP32 basis; BF16 and other workloads: null).
+GS_DRAM_CAPTURE = {("solve", "c64", 2): (3321.96e6 + 3.17e6 + 3322.40e6 + 98.07e6 + 3321.97e6 + 97.78e6,
+                                         3 * 3321.888768e6 + 2 * 100.663296e6)}
 
 
 def measured_peaks():

@@ -705,8 +705,12 @@ cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const d
 
 // x += sum_i y[i][r] v_i with the sum formed in the basis precision (the
 // correction of one restart cycle; its rounding is removed by the next FP64
-// true residual) and added to x in FP64.
-template <typename C, typename B>
+// true residual) and added to x in FP64. A CTA owns tiles of EPT * blockDim.x
+// consecutive elements and walks the vectors in the outer loop: per vector it reads
+// one contiguous run of the tile (EPT independent loads in flight per thread), with
+// the partial sums of its EPT elements in registers. blockDim.x is a multiple of
+// nrhs, so a thread's rhs (and its coefficients) are the same for all its elements.
+template <typename C, typename B, int EPT>
 __global__ void __launch_bounds__(256)
 update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstride,
                 const double2* __restrict__ y, const int* __restrict__ kmax, double2* __restrict__ x) {
@@ -717,40 +721,54 @@ update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstrid
   __syncthreads();
   if (k == 0) return;
   const int r = threadIdx.x % nrhs;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    // eight basis loads in flight per thread (independent partial sums), not a chain of k
-    Real sr[2] = {0, 0}, si[2] = {0, 0};
-#pragma unroll 8
+  const int64_t tile = (int64_t)blockDim.x * EPT;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+    Real sr[EPT], si[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) { sr[u] = 0; si[u] = 0; }
     for (int i = 0; i < k; ++i) {
       const double2 c = ys[i * nrhs + r];
-      const C v = C(ld_basis(basis + i * vstride + e));
       const Real crr = (Real)c.x, cii = (Real)c.y;
-      sr[i & 1] += crr * v.x - cii * v.y;
-      si[i & 1] += crr * v.y + cii * v.x;
+      const B* vi = basis + i * vstride + base + threadIdx.x;
+#pragma unroll
+      for (int u = 0; u < EPT; ++u) {
+        if (base + threadIdx.x + (int64_t)u * blockDim.x < n) {
+          const C v = C(ld_basis(vi + (int64_t)u * blockDim.x));
+          sr[u] += crr * v.x - cii * v.y;
+          si[u] += crr * v.y + cii * v.x;
+        }
+      }
     }
-    double2 xv = x[e];
-    xv.x += (double)(sr[0] + sr[1]);
-    xv.y += (double)(si[0] + si[1]);
-    x[e] = xv;
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int64_t e = base + threadIdx.x + (int64_t)u * blockDim.x;
+      if (e < n) {
+        double2 xv = x[e];
+        xv.x += (double)sr[u];
+        xv.y += (double)si[u];
+        x[e] = xv;
+      }
+    }
   }
 }
 
 cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
                             int64_t vstride, const void* y, const int* kmax, void* x,
                             cudaStream_t stream, bool basis_bf16) {
+  constexpr int EPT = 8;
   const int threads = nrhs * (256 / nrhs);
-  const int blocks = stream_blocks(n, threads);
+  int64_t tiles = (n + (int64_t)threads * EPT - 1) / ((int64_t)threads * EPT);
+  const int blocks = (int)(tiles < 1 ? 1 : (tiles > 152 * 8 ? 152 * 8 : tiles));
   const size_t smem = sizeof(double2) * (size_t)nvec_max * nrhs;
   if (basis_bf16)
-    update_x_kernel<float2, __nv_bfloat162><<<blocks, threads, smem, stream>>>(
+    update_x_kernel<float2, __nv_bfloat162, EPT><<<blocks, threads, smem, stream>>>(
         n, nrhs, (const __nv_bfloat162*)basis, vstride, (const double2*)y, kmax, (double2*)x);
   else if (basis_f64)
-    update_x_kernel<double2, double2><<<blocks, threads, smem, stream>>>(n, nrhs, (const double2*)basis, vstride,
-                                                                         (const double2*)y, kmax, (double2*)x);
+    update_x_kernel<double2, double2, EPT><<<blocks, threads, smem, stream>>>(
+        n, nrhs, (const double2*)basis, vstride, (const double2*)y, kmax, (double2*)x);
   else
-    update_x_kernel<float2, float2><<<blocks, threads, smem, stream>>>(n, nrhs, (const float2*)basis, vstride,
-                                                                       (const double2*)y, kmax, (double2*)x);
+    update_x_kernel<float2, float2, EPT><<<blocks, threads, smem, stream>>>(
+        n, nrhs, (const float2*)basis, vstride, (const double2*)y, kmax, (double2*)x);
   return cudaGetLastError();
 }
 

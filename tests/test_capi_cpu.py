@@ -73,3 +73,31 @@ def test_host_side_argument_errors(lib):
     assert b"twice" in lib.lqcd_last_error()
     assert lib.lqcd_free(h) == lq.OK
     assert lib.lqcd_free(None) == lq.OK
+
+
+def test_link_storage_variant_query_and_probe_arguments(lib):
+    """The link-storage switch, the variant link query and the FMA probe check their arguments on the host."""
+    import paper_2601_05816_gb300 as lq
+    h = ctypes.c_void_p()
+    assert lib.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), -1, ctypes.byref(h)) == lq.OK
+    assert lib.lqcd_get_link_storage(h) == lq.LINKS_FP32
+    assert lib.lqcd_set_link_storage(h, 7) == lq.ERR_ARG
+    assert lib.lqcd_set_link_storage(h, lq.LINKS_BF16) == lq.OK
+    assert lib.lqcd_get_link_storage(h) == lq.LINKS_BF16
+    assert lib.lqcd_set_link_storage(None, lq.LINKS_BF16) == lq.ERR_ARG
+    assert lib.lqcd_get_link_storage(None) == -1
+    n32 = lib.lqcd_kernel_variant_count(lq.C64)
+    reals = [lib.lqcd_kernel_variant_link_reals(lq.C64, v) for v in range(n32)]
+    assert set(reals) == {12, 18}
+    assert lib.lqcd_kernel_variant_link_reals(lq.C64, n32) == -1
+    assert lib.lqcd_kernel_variant_link_reals(9, 0) == -1
+    assert lib.lqcd_fma_peak(1, None, None) == lq.ERR_ARG
+    # block GMRES on a batch is refused before any device work
+    ctxs = (ctypes.c_void_p * 1)(h.value)
+    params = (lq.SolveParams * 1)()
+    params[0].block = 1
+    nr = (ctypes.c_int * 1)(2)
+    ptrs = (ctypes.c_void_p * 1)(16)
+    assert lib.lqcd_solve_batch(1, ctxs, params, nr, ptrs, ptrs, None, None) == lq.ERR_ARG
+    assert b"block" in lib.lqcd_last_error()
+    assert lib.lqcd_free(h) == lq.OK

@@ -537,3 +537,27 @@ def test_two_row_variants_read_fewer_link_bytes():
     reals = [lat.variant_link_reals(lq.C64, v) for v in range(lib.lqcd_kernel_variant_count(lq.C64))]
     assert set(reals) == {12, 18} and reals.count(12) >= 4
     assert all(lat.variant_link_reals(lq.C128, v) == 18 for v in range(lib.lqcd_kernel_variant_count(lq.C128)))
+
+
+@pytest.mark.parametrize("dtype", [lq.C64, lq.C128])
+@pytest.mark.parametrize("nrhs", [100, 256])
+def test_maximum_and_ragged_large_nrhs(dtype, nrhs):
+    """The largest rhs count an apply takes (256) and a large count that is no power of two (100): the
+    default launch and the tuned one, full and Schur, against the oracle."""
+    dims, kind, eps, m0, c_sw = CASES[0]
+    lat, U, C, A, Ainv = setup(dims, kind, eps, m0, c_sw, 101)
+    psi = syn.gaussian_spinors(dims, nrhs, 1000 + nrhs)
+    psi_o = oracle.split_parity(psi, 1)
+    ref_f = oracle.apply_D(U, psi, m0, C)
+    ref_s = oracle.apply_schur(U, A, Ainv, psi_o)
+    for tuned in (False, True):
+        if tuned:
+            lat.tune(dtype, nrhs, reps=1)
+        for op, src, ref in ((lq.OP_FULL, psi, ref_f), (lq.OP_SCHUR, psi_o, ref_s)):
+            d_in = dev(src, dtype)
+            d_out = torch.empty_like(d_in)
+            lat.apply(op, nrhs, d_in, d_out)
+            torch.cuda.synchronize()
+            assert relerr(d_out.cpu().numpy(), ref) < TOL[dtype], (op, tuned, lat.kernel_variant(dtype, nrhs, op))
+    for op in (lq.OP_FULL, lq.OP_SCHUR):
+        lat.set_kernel_variant(dtype, nrhs, op, -1)
