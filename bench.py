@@ -230,6 +230,40 @@ def oracle_apply_sample(w, nrhs: int):
             "setup_s": t_setup, "nrhs": nrhs}
 
 
+_POOL_STATE = {}
+
+
+def _oracle_pool_init(w):
+    """Worker set-up of the all-cores oracle sample: the workload's gauge field and site blocks."""
+    import oracle
+    import synthetic as syn
+    U = syn.gauge_field(w["dims"], "exp", w["eps"], seed=w["gauge_seed"])
+    A, Ainv = oracle.diag_blocks(U, w["m0"], w["c_sw"])
+    _POOL_STATE.update(U=U, A=A, Ainv=Ainv, dims=w["dims"])
+
+
+def _oracle_pool_apply(seed):
+    import oracle
+    import synthetic as syn
+    st = _POOL_STATE
+    psi_o = oracle.split_parity(syn.gaussian_spinors(st["dims"], 1, seed), 1)
+    oracle.apply_schur(st["U"], st["A"], st["Ainv"], psi_o)
+    return 1
+
+
+def oracle_apply_all_cores(w, cores):
+    """The oracle's Schur apply on one rhs per host core at once (processes started with spawn): site*rhs/s
+    of the whole host, timed over one round of `cores` applies after a warm-up round."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_pool_init, initargs=(w,)) as pool:
+        pool.map(_oracle_pool_apply, range(cores), chunksize=1)
+        t0 = time.perf_counter()
+        pool.map(_oracle_pool_apply, range(cores, 2 * cores), chunksize=1)
+        t = time.perf_counter() - t0
+    return V_of(w) // 2 * cores / t, t
+
+
 def cpu_threads():
     return int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
 
@@ -915,6 +949,18 @@ def extras_batch(args, lq, torch, line):
             out.append(lat.solve(b, x, n, **kw))
         return out
 
+    # each lattice alone: the largest of these bounds any concurrent schedule of the batch from below
+    alone = []
+    for lat, b, x, n in zip(lats, bs, xs, nr):
+        x.zero_()
+        lat.solve(b, x, n, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            x.zero_()
+            lat.solve(b, x, n, **kw)
+        torch.cuda.synchronize()
+        alone.append((time.perf_counter() - t0) / 3)
     res = {}
     for name, fn in (("batch", batch), ("sequential", sequential)):
         fn()
@@ -927,6 +973,7 @@ def extras_batch(args, lq, torch, line):
     tb, rb = res["batch"]
     ts, rs_ = res["sequential"]
     line["batch"] = {"workload": wb["name"], "batch_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+                     "alone_s": alone, "batch_over_largest_alone": tb / max(alone),
                      "site_rhs_per_s": units / tb, "iterations": [r.iterations for r in rb],
                      "relres_max": [r.relres_max for r in rb],
                      "status": [r.status for r in rb] + [r.status for r in rs_]}
@@ -995,8 +1042,18 @@ def extras_cpu_baseline(args, w, line, results):
     t_cyc = oracle_cycle(U, A, Ainv, b1, m)
     t_iter, t_fixed = oracle_cost_model(U, A, Ainv, b1, m, t_cyc)
     t_proj = t_setup + its_gpu * t_iter + -(-its_gpu // 32) * t_fixed
+    all_cores = None
+    if args.cpu_all_cores:
+        n = os.cpu_count() or 1
+        try:
+            v_all, t_all = oracle_apply_all_cores(w, n)
+            all_cores = {"value": v_all, "unit": "site·rhs/s (FP64 odd-even Schur apply)", "cores": n,
+                         "sample": f"{n} processes, one Schur apply on 1 rhs each at once ({t_all:.1f} s)"}
+        except Exception as exc:  # e.g. not enough host memory for one oracle per core
+            all_cores = {"unavailable": str(exc)[:200]}
     line["cpu_baseline"] = {
         "value": smp["schur"], "unit": "site·rhs/s (FP64 odd-even Schur apply)", "cores": cpu_threads(),
+        "all_cores": all_cores,
         "kind": "oracle",
         "sample": f"numpy FP64 oracle on the {w['name'].split(' ')[1]} lattice: one Schur apply and one full "
                   f"apply on {smp['nrhs']} Gaussian rhs, timed ({smp['schur_s']:.1f} s / {smp['full_s']:.1f} s; "
@@ -1023,6 +1080,8 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=535,
                     help="oracle arm: iterations per rhs of the GPU solve the oracle's cost is projected to")
     ap.add_argument("--cpu-nrhs", type=int, default=4, help="rhs of the timed oracle operator applies")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="1: also time the oracle's Schur apply on every host core at once (one process each)")
     ap.add_argument("--skip-large", action="store_true", help="skip the 32^3 x 64 GMRES comparison")
     ap.add_argument("--large-cap", type=int, default=64,
                     help="Arnoldi cycles allowed for the prescribed-mass 32^3 x 64 solve")
