@@ -414,7 +414,7 @@ def run_kernel_workload(args, w):
         vb = 4 if bf16 else 8
         nbytes = 3 * nvec * n * vb + n * 8 * 5
         launches = 7
-        kernel = f"gs_split_kernel ({'BF16' if bf16 else 'FP32'} basis; CGS2 step: dots, update+dots, update+norm)"
+        kernel = f"gs_stream_kernel ({'BF16' if bf16 else 'FP32'} basis; CGS2 step: dots, update+dots, update+norm)"
     for _ in range(args.warmup):
         step()
     s = torch.cuda.current_stream()

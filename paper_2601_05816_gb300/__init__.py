@@ -84,6 +84,7 @@ _SIGS = {
     "lqcd_set_link_storage": (_I, [_VP, _I]),
     "lqcd_fma_peak": (_I, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     "lqcd_kernel_variant_link_reals": (_I, [_I, _I]),
+    "lqcd_kernel_variant_shape": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int)]),
     "lqcd_get_link_storage": (_I, [_VP]),
 }
 
@@ -264,6 +265,10 @@ class Lattice:
         """Reals per link read by a hopping-kernel launch variant (18, or 12 with the third row rebuilt)."""
         return int(self._lib.lqcd_kernel_variant_link_reals(int(dtype), int(variant)))
 
+    def kernel_variant_info(self, dtype: int, variant: int) -> dict:
+        """Launch shape of a hopping-kernel variant (rhs per thread, threads, ..., blocked row order)."""
+        return variant_shape(dtype, variant)
+
     def kernel_variant(self, dtype: int, nrhs: int, op: int) -> int:
         return int(self._lib.lqcd_get_kernel_variant(self._h, int(dtype), int(nrhs), int(op)))
 
@@ -332,6 +337,17 @@ def fma_peak(f64: bool, stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(load().lqcd_fma_peak(int(bool(f64)), ctypes.byref(v), _stream(stream)), "lqcd_fma_peak")
     return float(v.value)
+
+
+_SHAPE_KEYS = ("nr", "threads", "min_ctas", "stages", "nrhs_fixed", "prefetch", "ring_warps", "ring_slots",
+               "link_reals", "order")
+
+
+def variant_shape(dtype: int, variant: int) -> dict:
+    """Launch shape of a hopping-kernel variant (lqcd_kernel_variant_shape), keyed by field name."""
+    shape = (ctypes.c_int * 10)()
+    _check(load().lqcd_kernel_variant_shape(int(dtype), int(variant), shape), "lqcd_kernel_variant_shape")
+    return dict(zip(_SHAPE_KEYS, (int(x) for x in shape)))
 
 
 def solve_batch(lattices, bs, xs, nrhs, *, op: int = OP_SCHUR, precision: int = C64, restart_len: int = 32,

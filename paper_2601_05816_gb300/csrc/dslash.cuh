@@ -67,6 +67,8 @@ struct DslashArgs {
   const void* links_r12;       // [4][6][V] float2: rows 0, 1 of each packed link
   const void* links_r12_bf16;  // [4][6][V] BF16 pairs: the same rows rounded to BF16
   int link_format;             // 0: 18-real FP32 links (links); 2: 12-real BF16 (links_r12_bf16)
+  int blk_rz;                  // > 0: blocked site mapping (ORD = 1 variants, one parity): a CTA takes the
+                               // target rows (t, z0 .. z0 + blk_rz - 1, y0 .. y0 + 1); set by the launcher
   Real time_bc;                // fermion time boundary factor (+1 / -1)
 };
 
@@ -349,18 +351,20 @@ __device__ __forceinline__ void prefetch_dir(const DslashArgs<Real>& a, const Co
   }
 }
 
-// Direction K = 0..7 of the hopping sum: mu = K / 2, forward for even K.
-template <int K> struct DirOf {
-  static constexpr int MU = K / 2;
+// Direction K = 0..7 of the hopping sum, forward for even K: mu = K / 2 in order t, z, y, x
+// (ORD = 0) or mu = 3 - K / 2 in order x, y, z, t (ORD = 1: the directions whose neighbour
+// spinors the CTA's other rows share come first, while they are still in L1).
+template <int K, int ORD = 0> struct DirOf {
+  static constexpr int MU = ORD == 0 ? K / 2 : 3 - K / 2;
   static constexpr int DIR = (K % 2 == 0) ? +1 : -1;
 };
 
-template <typename Real, int NR, bool BATCH, typename HIN, int NRHS, int PF, int K, int LF = 0>
+template <typename Real, int NR, bool BATCH, typename HIN, int NRHS, int PF, int K, int LF = 0, int ORD = 0>
 __device__ __forceinline__ void hop_step(const DslashArgs<Real>& a, const Coord& c, int p, int r0, const HIN* hin,
                                          MC<Real, NR> acc[12]) {
   if constexpr (PF > 0 && K + PF < 8)
-    prefetch_dir<Real, NR, DirOf<K + PF>::MU, DirOf<K + PF>::DIR, HIN, NRHS>(a, c, p, hin);
-  hop_dir<Real, NR, DirOf<K>::MU, DirOf<K>::DIR, BATCH, HIN, NRHS, LF>(a, c, p, r0, hin, acc);
+    prefetch_dir<Real, NR, DirOf<K + PF, ORD>::MU, DirOf<K + PF, ORD>::DIR, HIN, NRHS>(a, c, p, hin);
+  hop_dir<Real, NR, DirOf<K, ORD>::MU, DirOf<K, ORD>::DIR, BATCH, HIN, NRHS, LF>(a, c, p, r0, hin, acc);
 }
 
 // Packed Hermitian 6x6 block: 6 real diagonal entries, then the 15 strictly
@@ -427,7 +431,7 @@ __device__ __forceinline__ void site_block_apply(const Real* blocks, int V, int 
 
 // The whole operator on one target site for this thread's NR rhs.
 template <typename Real, int NR, int SELF, int POST, bool BATCH, typename HIN, typename SIN, int NRHS = 0, int PF = 0,
-          int LF = 0>
+          int LF = 0, int ORD = 0>
 __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site) {
   using C = typename Cplx<Real>::T;
   const int r0 = threadIdx.x * NR;
@@ -449,17 +453,17 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
     const Coord c = site_coords(a.g, p, cb);
     const HIN* hin = reinterpret_cast<const HIN*>(a.hop_in) + (a.full ? (1 - p) * a.half_elems : 0);
     if constexpr (PF > 0) {
-      prefetch_dir<Real, NR, 0, +1, HIN, NRHS>(a, c, p, hin);
-      if constexpr (PF > 1) prefetch_dir<Real, NR, 0, -1, HIN, NRHS>(a, c, p, hin);
+      prefetch_dir<Real, NR, DirOf<0, ORD>::MU, +1, HIN, NRHS>(a, c, p, hin);
+      if constexpr (PF > 1) prefetch_dir<Real, NR, DirOf<1, ORD>::MU, -1, HIN, NRHS>(a, c, p, hin);
     }
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 0, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 1, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 2, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 3, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 4, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 5, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 6, LF>(a, c, p, r0, hin, acc);
-    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 7, LF>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 0, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 1, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 2, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 3, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 4, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 5, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 6, LF, ORD>(a, c, p, r0, hin, acc);
+    hop_step<Real, NR, BATCH, HIN, NRHS, PF, 7, LF, ORD>(a, c, p, r0, hin, acc);
 #pragma unroll
     for (int k = 0; k < 12; ++k)
 #pragma unroll
@@ -509,12 +513,25 @@ __device__ __forceinline__ void dslash_site(const DslashArgs<Real>& a, int site)
 }
 
 template <typename Real, int NR, int SELF, int POST, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0, int PF = 0, int LF = 0>
+          typename SIN, int NRHS = 0, int PF = 0, int LF = 0, int ORD = 0>
 __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) {
   if (a.skip != nullptr && *a.skip != 0) return;
   if (!LOOP) {
-    const int site = blockIdx.x * blockDim.y + threadIdx.y;
-    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF>(a, site);
+    int site = blockIdx.x * blockDim.y + threadIdx.y;
+    if (ORD == 1 && a.blk_rz > 0) {
+      // blocked mapping (one parity): the CTA's targets are the X/2 targets of each of the rows
+      // (t, z0 + dz, y0 + dy), dz < blk_rz, dy < 2, so the rows' shared neighbour spinors meet in L1
+      const int hx = a.g.X >> 1;
+      const int xi = threadIdx.y % hx, row = threadIdx.y / hx;
+      const int ny = a.g.Y >> 1, nz = a.g.Z / a.blk_rz;
+      int b = blockIdx.x;
+      const int yb = b % ny;
+      b /= ny;
+      const int zb = b % nz, t = b / nz;
+      const int z = zb * a.blk_rz + (row >> 1), y = yb * 2 + (row & 1);
+      site = ((((t * a.g.Z + z) * a.g.Y + y) * a.g.X) >> 1) + xi;
+    }
+    if (site < a.n_target) dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF, ORD>(a, site);
     return;
   }
   // persistent CTAs: each walks one contiguous chunk of target sites, blockDim.y
@@ -523,7 +540,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_kernel(DslashArgs<Real> a) 
   const int s0 = blockIdx.x * a.loop_chunk;
   const int s1 = min(s0 + a.loop_chunk, a.n_target);
   for (int site = s0 + threadIdx.y; site < s1; site += blockDim.y)
-    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF>(a, site);
+    dslash_site<Real, NR, SELF, POST, BATCH, HIN, SIN, NRHS, PF, LF, ORD>(a, site);
 }
 
 // Launch variants of the kernel: rhs per thread (NR), threads per CTA (the CTA is
@@ -540,6 +557,7 @@ struct DslashVariant {
   int ring_warps = 0;  // > 0: the bulk-copy ring kernel (dslash_ring.cuh) with this many warps per CTA
   int ring_slots = 0;  //       and this many ring slots per warp
   int links = 0;       // 1: reads the 12-real FP32 link copy (third row rebuilt)
+  int order = 0;       // 1: directions x, y, z, t and the blocked site mapping (one CTA per row block)
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);
@@ -552,10 +570,19 @@ cudaError_t launch_dslash(const DslashArgs<Real>& a, int self_mode, int post_mod
 
 // Launch one (SELF, POST) combination of one variant; defined by LQCD_DSLASH_VARIANT_TU.
 template <typename Real, int NR, int SM, int PM, int MAXT, int MINB, bool BATCH, bool LOOP, typename HIN,
-          typename SIN, int NRHS = 0, int PF = 0, int LF = 0>
+          typename SIN, int NRHS = 0, int PF = 0, int LF = 0, int ORD = 0>
 cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
-  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF>;
+  auto kern = dslash_kernel<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF, ORD>;
   dim3 grid((a.n_target + block.y - 1) / block.y);
+  a.blk_rz = 0;
+  if (ORD == 1 && !LOOP && !a.full) {
+    // the blocked mapping needs whole rows per CTA, an even row count and z blocks that tile Z
+    const int hx = a.g.X / 2;
+    const int rows = hx > 0 && (int)block.y % hx == 0 ? (int)block.y / hx : 0;
+    if (rows >= 2 && rows % 2 == 0 && a.g.X % 2 == 0 && a.g.Y % 2 == 0 && a.g.Z % (rows / 2) == 0 &&
+        a.n_target == a.g.Vh && (int)grid.x * (int)block.y == a.n_target)
+      a.blk_rz = rows / 2;
+  }
   if (PF > 0) {
     // the prefetched lines live in L1: ask for the smallest shared-memory carve-out
     static std::once_flag carveout;
@@ -584,7 +611,7 @@ cudaError_t launch_dslash_one(DslashArgs<Real> a, dim3 block, cudaStream_t s) {
 
 template <typename Real, int NR, int MAXT, int MINB, bool BATCH, bool LOOP = false,
           typename HIN = typename Cplx<Real>::T, typename SIN = typename Cplx<Real>::T, int NRHS = 0, int PF = 0,
-          int LF = 0>
+          int LF = 0, int ORD = 0>
 cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int post_mode, cudaStream_t s) {
   if (NRHS > 0 && (a.lay.nrhs != NRHS || a.lay.log_s != 0)) return cudaErrorInvalidValue;
   if (LF == 1 && a.links_r12 == nullptr) return cudaErrorInvalidValue;
@@ -592,7 +619,7 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
   const int G = a.lay.nrhs / NR;
   dim3 block(G, G >= MAXT ? 1 : MAXT / G);
 #define LQCD_DS(SM, PM) \
-  return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF>(a, block, s)
+  return launch_dslash_one<Real, NR, SM, PM, MAXT, MINB, BATCH, LOOP, HIN, SIN, NRHS, PF, LF, ORD>(a, block, s)
   if (self_mode == SELF_SCALAR && post_mode == POST_NONE) LQCD_DS(SELF_SCALAR, POST_NONE);
   else if (self_mode == SELF_BLOCK && post_mode == POST_NONE) LQCD_DS(SELF_BLOCK, POST_NONE);
   else if (self_mode == SELF_NONE && post_mode == POST_SCALAR) LQCD_DS(SELF_NONE, POST_SCALAR);
@@ -615,6 +642,11 @@ cudaError_t launch_dslash_variant(const DslashArgs<Real>& a, int self_mode, int 
 // ... and of an FP32 variant reading two-row links (LF = 1: FP32 rows, 2: BF16 rows).
 #define LQCD_DSLASH_VARIANT_LF_TU(NR, MAXT, MINB, LOOP, NRHS, PF, LF)                                      \
   template cudaError_t launch_dslash_variant<float, NR, MAXT, MINB, false, LOOP, float2, float2, NRHS, PF, LF>( \
+      const DslashArgs<float>&, int, int, cudaStream_t);
+
+// ... and of an FP32 variant with the blocked mapping and the x, y, z, t direction order.
+#define LQCD_DSLASH_VARIANT_ORD_TU(NR, MAXT, MINB, NRHS, PF)                                                  \
+  template cudaError_t launch_dslash_variant<float, NR, MAXT, MINB, false, false, float2, float2, NRHS, PF, 0, 1>( \
       const DslashArgs<float>&, int, int, cudaStream_t);
 
 // FP32 arithmetic on BF16-stored inputs (hop input HIN, self-term input SIN), FP32 output.

@@ -7,7 +7,7 @@ namespace lqcd {
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
 //  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance,
-//  ring kernel warps per CTA, ring slots per warp, two-row links}
+//  ring kernel warps per CTA, ring slots per warp, two-row links, blocked rows + x, y, z, t order}
 const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
                              {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16},
                              {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
@@ -24,7 +24,10 @@ const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 12
                              // two-row FP32 links (third row rebuilt)
                              {1, 256, 1, 0, 0, 0, 0, 0, 0, 0, 1}, {2, 256, 2, 0, 0, 0, 0, 0, 0, 0, 1},
                              {2, 128, 4, 0, 0, 0, 0, 0, 0, 0, 1}, {2, 256, 2, 0, 0, 1, 0, 0, 0, 0, 1},
-                             {2, 128, 4, 0, 0, 0, 16, 2, 0, 0, 1}};
+                             {2, 128, 4, 0, 0, 0, 16, 2, 0, 0, 1},
+                             // blocked rows per CTA, directions x, y, z, t
+                             {2, 512, 1, 0, 0, 0, 16, 0, 0, 0, 0, 1}, {2, 512, 1, 0, 0, 0, 16, 2, 0, 0, 0, 1},
+                             {2, 256, 2, 0, 0, 0, 16, 2, 0, 0, 0, 1}, {2, 512, 1, 0, 0, 0, 32, 2, 0, 0, 0, 1}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -67,6 +70,14 @@ LQCD_EXTERN_LF(2, 128, 4, false, 0, 0, 2)
 LQCD_EXTERN_LF(2, 256, 2, true, 0, 0, 2)
 LQCD_EXTERN_LF(2, 128, 4, false, 16, 2, 2)
 #undef LQCD_EXTERN_LF
+#define LQCD_EXTERN_ORD(NR, MAXT, MINB, NRHS, PF)                                                              \
+  extern template cudaError_t launch_dslash_variant<float, NR, MAXT, MINB, false, false, float2, float2, NRHS, PF, 0, 1>( \
+      const DslashArgs<float>&, int, int, cudaStream_t);
+LQCD_EXTERN_ORD(2, 512, 1, 16, 0)
+LQCD_EXTERN_ORD(2, 512, 1, 16, 2)
+LQCD_EXTERN_ORD(2, 256, 2, 16, 2)
+LQCD_EXTERN_ORD(2, 512, 1, 32, 2)
+#undef LQCD_EXTERN_ORD
 extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
@@ -150,6 +161,10 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
     case 35: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
     case 36: return launch_dslash_variant<float, 2, 256, 2, false, true, float2, float2, 0, 0, 1>(a, self_mode, post_mode, s);
     case 37: return launch_dslash_variant<float, 2, 128, 4, false, false, float2, float2, 16, 2, 1>(a, self_mode, post_mode, s);
+    case 38: return launch_dslash_variant<float, 2, 512, 1, false, false, float2, float2, 16, 0, 0, 1>(a, self_mode, post_mode, s);
+    case 39: return launch_dslash_variant<float, 2, 512, 1, false, false, float2, float2, 16, 2, 0, 1>(a, self_mode, post_mode, s);
+    case 40: return launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16, 2, 0, 1>(a, self_mode, post_mode, s);
+    case 41: return launch_dslash_variant<float, 2, 512, 1, false, false, float2, float2, 32, 2, 0, 1>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -97,6 +97,17 @@ __device__ __forceinline__ void stg(__nv_bfloat162* p, const float2 (&v)[EPL]) {
   }
 }
 
+// acc += c v and (re, im) += conj(v) w as chains of fused multiply-adds (four per complex
+// product, no separate multiply or add)
+__device__ __forceinline__ void cmac(float2 c, float2 v, float2& acc) {
+  acc.x = fmaf(-c.y, v.y, fmaf(c.x, v.x, acc.x));
+  acc.y = fmaf(c.y, v.x, fmaf(c.x, v.y, acc.y));
+}
+__device__ __forceinline__ void cdot(float2 v, float2 w, float& re, float& im) {
+  re = fmaf(v.y, w.y, fmaf(v.x, w.x, re));
+  im = fmaf(-v.y, w.x, fmaf(v.x, w.y, im));
+}
+
 constexpr int kConsumers = 8;                 // consumer warps
 constexpr int kThreads = 32 * (kConsumers + 1);
 
@@ -241,10 +252,8 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               lds<1>(vt + (size_t)i * vte + eA, va);
               if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
               const C c = cr[k];
-              sa[k & 1].x += c.x * va[0].x - c.y * va[0].y;
-              sa[k & 1].y += c.x * va[0].y + c.y * va[0].x;
-              sb[k & 1].x += c.x * vb[0].x - c.y * vb[0].y;
-              sb[k & 1].y += c.x * vb[0].y + c.y * vb[0].x;
+              cmac(c, va[0], sa[k & 1]);
+              cmac(c, vb[0], sb[k & 1]);
             }
           }
           const C pa = make_float2(sa[0].x + sa[1].x, sa[0].y + sa[1].y);
@@ -258,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
             const C ws[1] = {make_float2(wn.x * sc[0], wn.y * sc[0])};
             if (a.wout != nullptr) stg<1>((B*)a.wout + row0 * nrhs + e, ws);
             else stg<1>(w + row0 * nrhs + e, ws);
-            if (NORM) nn[0] += wn.x * wn.x + wn.y * wn.y;
+            if (NORM) nn[0] = fmaf(wn.y, wn.y, fmaf(wn.x, wn.x, nn[0]));
           }
           // dots of this lane's vectors with the updated w of both rows
           const float wx = __shfl_sync(0xffffffffu, wn.x, partner);
@@ -273,8 +282,8 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               C va[1], vb[1] = {make_float2(0.f, 0.f)};
               lds<1>(vt + (size_t)i * vte + eA, va);
               if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
-              ar[k][0] += (va[0].x * wa.x + va[0].y * wa.y) + (vb[0].x * wb.x + vb[0].y * wb.y);
-              ai[k][0] += (va[0].x * wa.y - va[0].y * wa.x) + (vb[0].x * wb.y - vb[0].y * wb.x);
+              cdot(va[0], wa, ar[k][0], ai[k][0]);
+              cdot(vb[0], wb, ar[k][0], ai[k][0]);
             }
           }
         }
@@ -301,8 +310,10 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
 #pragma unroll
               for (int q = 0; q < EPL; ++q) {
                 const C c = kCoefRegs ? cr[i < NC ? i : 0] : cs[i * nrhs + r + q];
-                pr[i & 3][q] += c.x * v[q].x - c.y * v[q].y;
-                pi[i & 3][q] += c.x * v[q].y + c.y * v[q].x;
+                C acc = make_float2(pr[i & 3][q], pi[i & 3][q]);
+                cmac(c, v[q], acc);
+                pr[i & 3][q] = acc.x;
+                pi[i & 3][q] = acc.y;
               }
             }
           }
@@ -319,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
         }
         if (NORM) {
 #pragma unroll
-          for (int q = 0; q < EPL; ++q) nn[q] += wn[q].x * wn[q].x + wn[q].y * wn[q].y;
+          for (int q = 0; q < EPL; ++q) nn[q] = fmaf(wn[q].y, wn[q].y, fmaf(wn[q].x, wn[q].x, nn[q]));
         }
         if (DOTS) {
 #pragma unroll
@@ -328,10 +339,7 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               C v[EPL];
               lds<EPL>(vt + (size_t)i * vte + e, v);
 #pragma unroll
-              for (int q = 0; q < EPL; ++q) {
-                ar[i][q] += v[q].x * wn[q].x + v[q].y * wn[q].y;
-                ai[i][q] += v[q].x * wn[q].y - v[q].y * wn[q].x;
-              }
+              for (int q = 0; q < EPL; ++q) cdot(v[q], wn[q], ar[i][q], ai[i][q]);
             }
           }
         }
@@ -435,15 +443,14 @@ inline Plan make_plan(int nrhs, int nvec, int nv, int epl, int elem_bytes, bool 
     const size_t st = (size_t)S * stage > red_one ? (size_t)S * stage : red_one;
     return p.stage_off + st <= budget;
   };
-  // up to 4 (two CTAs per SM) or 6 stages; the largest tile with a stage of at most
-  // 32 KB, else the smallest tile (8 warps x H rows) if it fits
-  for (int S = two ? 4 : 6; S >= 2; --S) {
+  // three stages (two where three do not fit) of the largest tile that fits: the larger
+  // the tile, the larger each vector's bulk copy and the fewer copies per byte (a copy of
+  // the 16-row minimum tile of a BF16 basis is only 1 KB, and the copy count, not the
+  // bytes, then set the pace of the pass)
+  for (int S = 3; S >= 2; --S) {
     int best = 0;
-    for (int J = jstep; J <= 64; J += jstep) {
-      uint32_t vt;
-      if (fits(J, S) && stage_of(J, &vt) <= 32 * 1024) best = J;
-    }
-    if (best == 0 && fits(jstep, S)) best = jstep;
+    for (int J = jstep; J <= 64; J += jstep)
+      if (fits(J, S)) best = J;
     if (best > 0) {
       p.J = best;
       p.S = S;

@@ -92,6 +92,15 @@ def test_link_storage_variant_query_and_probe_arguments(lib):
     assert lib.lqcd_kernel_variant_link_reals(lq.C64, n32) == -1
     assert lib.lqcd_kernel_variant_link_reals(9, 0) == -1
     assert lib.lqcd_fma_peak(1, None, None) == lq.ERR_ARG
+    # the shape query agrees with the link query and marks the blocked-row variants
+    shapes = [lq.variant_shape(lq.C64, v) for v in range(n32)]
+    assert [sh["link_reals"] for sh in shapes] == reals
+    blocked = [sh for sh in shapes if sh["order"] == 1]
+    assert blocked and all(sh["ring_warps"] == 0 and sh["stages"] == 0 and sh["nrhs_fixed"] > 0 for sh in blocked)
+    assert all(sh["order"] == 0 for sh in (lq.variant_shape(lq.C128, v)
+                                           for v in range(lib.lqcd_kernel_variant_count(lq.C128))))
+    assert lib.lqcd_kernel_variant_shape(lq.C64, n32, (ctypes.c_int * 10)()) == lq.ERR_ARG
+    assert lib.lqcd_kernel_variant_shape(lq.C64, 0, None) == lq.ERR_ARG
     # block GMRES on a batch is refused before any device work
     ctxs = (ctypes.c_void_p * 1)(h.value)
     params = (lq.SolveParams * 1)()

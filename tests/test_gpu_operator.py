@@ -392,6 +392,46 @@ def test_every_kernel_variant_and_tuner(dtype):
         assert lat.kernel_variant(d, n, o) == saved[f"{d},{n},{o}"]
 
 
+@pytest.mark.parametrize("nrhs", [16, 32])
+def test_blocked_row_variants(nrhs):
+    """The variants that give each CTA a block of target rows (t, z0 .. z0 + rz - 1, y0, y0 + 1) and walk the
+    directions x, y, z, t: on a lattice whose shape lets every such launch take the blocked mapping (whole
+    x rows per CTA, z blocks tiling Z), the Schur operator and both single-parity hopping passes agree with
+    the oracle element-wise; the full operator (both parities, linear mapping) too."""
+    dims = (4, 8, 4, 8)       # T, Z, Y, X: X/2 = 4 targets per row
+    lat, U, C, A, Ainv = setup(dims, "exp", 0.4, -0.1, 1.0, 303)
+    lib = lq.load()
+    T, Z, Y, X = dims
+    psi = syn.gaussian_spinors(dims, nrhs, 900 + nrhs)
+    psi_o = oracle.split_parity(psi, 1)
+    ref_f = oracle.apply_D(U, psi, -0.1, C)
+    ref_s = oracle.apply_schur(U, A, Ainv, psi_o)
+    ran = 0
+    for v in range(lib.lqcd_kernel_variant_count(lq.C64)):
+        info = lat.kernel_variant_info(lq.C64, v)
+        if info["order"] != 1:
+            continue
+        lanes = nrhs // info["nr"]
+        targets = info["threads"] // lanes
+        rows = targets // (X // 2)
+        # the precondition of the blocked mapping holds on this lattice
+        assert targets % (X // 2) == 0 and rows % 2 == 0 and Z % (rows // 2) == 0
+        for op, src, ref in ((lq.OP_FULL, psi, ref_f), (lq.OP_SCHUR, psi_o, ref_s)):
+            try:
+                lat.set_kernel_variant(lq.C64, nrhs, op, v)
+            except lq.LqcdError:
+                continue
+            d_in = dev(src, lq.C64)
+            d_out = torch.empty_like(d_in)
+            lat.apply(op, nrhs, d_in, d_out)
+            torch.cuda.synchronize()
+            assert relerr(d_out.cpu().numpy(), ref) < TOL[lq.C64], (v, op)
+            ran += 1
+    for op in (lq.OP_FULL, lq.OP_SCHUR):
+        lat.set_kernel_variant(lq.C64, nrhs, op, -1)
+    assert ran >= (6 if nrhs == 16 else 2)
+
+
 def _bf16_round(a):
     """Round a complex array to BF16 real and imaginary parts (round to nearest even), back to complex128."""
     t = torch.from_numpy(np.ascontiguousarray(a)).to(torch.complex64)
