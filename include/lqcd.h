@@ -171,14 +171,16 @@ int lqcd_kernel_variant_count(lqcd_dtype dtype);
 /* Reals per link a launch variant reads (18, or 12 for the two-row copy whose third row the
  * kernel rebuilds; either way the same operator to rounding); -1 on bad arguments. */
 int lqcd_kernel_variant_link_reals(lqcd_dtype dtype, int variant);
-/* Launch shape of a hopping-kernel variant, written to the caller's host array shape[10]:
+/* Launch shape of a hopping-kernel variant, written to the caller's host array shape[11]:
  * [0] rhs per thread, [1] threads per CTA, [2] minimum resident CTAs per SM, [3] cp.async
  * stages (0: direct loads), [4] rhs count it is compiled for (0: any), [5] L1 prefetch
  * distance in directions, [6] ring-kernel warps per CTA (0: register kernel), [7] ring slots
  * per warp, [8] reals per link, [9] 1 where a single-parity launch gives each CTA a block of
  * target rows (t, z0 .. z0 + rz - 1, y0, y0 + 1) and walks the directions x, y, z, t (the
  * mapping is taken when whole x rows fill the CTA, rz = targets per CTA / X and rz divides Z;
- * else the plain linear site order). LQCD_ERR_ARG on a bad dtype, variant or null pointer. */
+ * else the plain linear site order), [10] cp.async stages of the pipelined kernel (0: not that
+ * kernel), which copies each thread's operands of the next directions into shared memory.
+ * LQCD_ERR_ARG on a bad dtype, variant or null pointer. */
 lqcd_status lqcd_kernel_variant_shape(lqcd_dtype dtype, int variant, int* shape);
 int lqcd_get_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op);
 lqcd_status lqcd_set_kernel_variant(lqcd_ctx ctx, lqcd_dtype dtype, int nrhs, lqcd_op op, int variant);

@@ -340,12 +340,12 @@ def fma_peak(f64: bool, stream=None) -> float:
 
 
 _SHAPE_KEYS = ("nr", "threads", "min_ctas", "stages", "nrhs_fixed", "prefetch", "ring_warps", "ring_slots",
-               "link_reals", "order")
+               "link_reals", "order", "pipe")
 
 
 def variant_shape(dtype: int, variant: int) -> dict:
     """Launch shape of a hopping-kernel variant (lqcd_kernel_variant_shape), keyed by field name."""
-    shape = (ctypes.c_int * 10)()
+    shape = (ctypes.c_int * 11)()
     _check(load().lqcd_kernel_variant_shape(int(dtype), int(variant), shape), "lqcd_kernel_variant_shape")
     return dict(zip(_SHAPE_KEYS, (int(x) for x in shape)))
 

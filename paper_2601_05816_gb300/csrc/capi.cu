@@ -601,9 +601,9 @@ lqcd_status lqcd_kernel_variant_shape(lqcd_dtype dtype, int variant, int* shape)
   if (!valid_dtype(dtype) || shape == nullptr || variant < 0 || variant >= dslash_variant_count(dtype == LQCD_C128))
     return set_error(LQCD_ERR_ARG, "lqcd_kernel_variant_shape: bad dtype, variant or null shape");
   const DslashVariant v = dslash_variant(dtype == LQCD_C128, variant);
-  const int f[10] = {v.nr, v.threads, v.minb, v.stages, v.nrhs_fixed, v.prefetch, v.ring_warps, v.ring_slots,
-                     v.links == 1 ? 12 : 18, v.order};
-  for (int i = 0; i < 10; ++i) shape[i] = f[i];
+  const int f[11] = {v.nr, v.threads, v.minb, v.stages, v.nrhs_fixed, v.prefetch, v.ring_warps, v.ring_slots,
+                     v.links == 1 ? 12 : 18, v.order, v.pipe};
+  for (int i = 0; i < 11; ++i) shape[i] = f[i];
   return LQCD_OK;
 }
 

@@ -558,6 +558,7 @@ struct DslashVariant {
   int ring_slots = 0;  //       and this many ring slots per warp
   int links = 0;       // 1: reads the 12-real FP32 link copy (third row rebuilt)
   int order = 0;       // 1: directions x, y, z, t and the blocked site mapping (one CTA per row block)
+  int pipe = 0;        // > 0: the pipelined kernel (dslash_pipe.cuh) with this many cp.async stages
 };
 int dslash_variant_count(bool f64);
 DslashVariant dslash_variant(bool f64, int idx);

@@ -1,13 +1,15 @@
 // Variant tables and dispatch of the multi-rhs hopping kernel.
 #include "dslash_async.cuh"
 #include "dslash_ring.cuh"
+#include "dslash_pipe.cuh"
 
 namespace lqcd {
 
 namespace {
 // {rhs per thread, threads per CTA, min CTAs per SM, cp.async stages (0 = direct loads),
 //  batched loads, persistent chunk loop, rhs count fixed at compile time, L1 prefetch distance,
-//  ring kernel warps per CTA, ring slots per warp, two-row links, blocked rows + x, y, z, t order}
+//  ring kernel warps per CTA, ring slots per warp, two-row links, blocked rows + x, y, z, t order,
+//  pipelined kernel stages}
 const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 128, 1, 0, 0, 0}, {1, 128, 6, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {2, 256, 2, 0, 0, 0}, {2, 128, 1, 2, 0, 0}, {2, 128, 4, 0, 1, 0}, {2, 64, 8, 0, 1, 0}, {2, 128, 4, 0, 0, 1}, {2, 128, 4, 0, 1, 1}, {2, 256, 2, 0, 0, 1}, {1, 128, 6, 0, 0, 1},
                              {2, 128, 4, 0, 0, 0, 16}, {2, 256, 2, 0, 0, 0, 16},
                              {2, 128, 4, 0, 0, 0, 16, 1}, {2, 128, 4, 0, 0, 0, 16, 2}, {2, 256, 2, 0, 0, 0, 16, 1},
@@ -27,7 +29,12 @@ const DslashVariant kF32[] = {{2, 128, 1, 0, 0, 0}, {2, 128, 4, 0, 0, 0}, {1, 12
                              {2, 128, 4, 0, 0, 0, 16, 2, 0, 0, 1},
                              // blocked rows per CTA, directions x, y, z, t
                              {2, 512, 1, 0, 0, 0, 16, 0, 0, 0, 0, 1}, {2, 512, 1, 0, 0, 0, 16, 2, 0, 0, 0, 1},
-                             {2, 256, 2, 0, 0, 0, 16, 2, 0, 0, 0, 1}, {2, 512, 1, 0, 0, 0, 32, 2, 0, 0, 0, 1}};
+                             {2, 256, 2, 0, 0, 0, 16, 2, 0, 0, 0, 1}, {2, 512, 1, 0, 0, 0, 32, 2, 0, 0, 0, 1},
+                             // pipelined kernel (dslash_pipe.cuh): operands one or two directions ahead in
+                             // shared memory, copied by each thread with cp.async
+                             {2, 128, 4, 0, 0, 0, 16, 0, 0, 0, 0, 0, 2}, {2, 128, 2, 0, 0, 0, 16, 0, 0, 0, 0, 0, 3},
+                             {2, 256, 2, 0, 0, 0, 16, 0, 0, 0, 0, 0, 2}, {2, 128, 4, 0, 0, 0, 32, 0, 0, 0, 0, 0, 2},
+                             {2, 128, 4, 0, 0, 0, 64, 0, 0, 0, 0, 0, 2}};
 const DslashVariant kF64[] = {{1, 128, 1, 0, 0, 0}, {1, 128, 4, 0, 0, 0}, {1, 256, 1, 0, 0, 0}, {1, 64, 1, 0, 0, 0}, {1, 128, 1, 2, 0, 0}, {1, 128, 4, 0, 1, 0}, {1, 128, 4, 0, 0, 1}};
 }  // namespace
 
@@ -78,6 +85,11 @@ LQCD_EXTERN_ORD(2, 512, 1, 16, 2)
 LQCD_EXTERN_ORD(2, 256, 2, 16, 2)
 LQCD_EXTERN_ORD(2, 512, 1, 32, 2)
 #undef LQCD_EXTERN_ORD
+extern template cudaError_t launch_dslash_pipe<16, 128, 4, 2>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_pipe<16, 128, 2, 3>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_pipe<16, 256, 2, 2>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_pipe<32, 128, 4, 2>(const DslashArgs<float>&, int, int, cudaStream_t);
+extern template cudaError_t launch_dslash_pipe<64, 128, 4, 2>(const DslashArgs<float>&, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<16>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<32>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_dslash_ring<64>(const DslashArgs<float>&, int, int, int, int, int, cudaStream_t);
@@ -165,6 +177,11 @@ cudaError_t launch_dslash<float>(const DslashArgs<float>& a, int self_mode, int 
     case 39: return launch_dslash_variant<float, 2, 512, 1, false, false, float2, float2, 16, 2, 0, 1>(a, self_mode, post_mode, s);
     case 40: return launch_dslash_variant<float, 2, 256, 2, false, false, float2, float2, 16, 2, 0, 1>(a, self_mode, post_mode, s);
     case 41: return launch_dslash_variant<float, 2, 512, 1, false, false, float2, float2, 32, 2, 0, 1>(a, self_mode, post_mode, s);
+    case 42: return launch_dslash_pipe<16, 128, 4, 2>(a, self_mode, post_mode, s);
+    case 43: return launch_dslash_pipe<16, 128, 2, 3>(a, self_mode, post_mode, s);
+    case 44: return launch_dslash_pipe<16, 256, 2, 2>(a, self_mode, post_mode, s);
+    case 45: return launch_dslash_pipe<32, 128, 4, 2>(a, self_mode, post_mode, s);
+    case 46: return launch_dslash_pipe<64, 128, 4, 2>(a, self_mode, post_mode, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -99,7 +99,9 @@ def test_link_storage_variant_query_and_probe_arguments(lib):
     assert blocked and all(sh["ring_warps"] == 0 and sh["stages"] == 0 and sh["nrhs_fixed"] > 0 for sh in blocked)
     assert all(sh["order"] == 0 for sh in (lq.variant_shape(lq.C128, v)
                                            for v in range(lib.lqcd_kernel_variant_count(lq.C128))))
-    assert lib.lqcd_kernel_variant_shape(lq.C64, n32, (ctypes.c_int * 10)()) == lq.ERR_ARG
+    assert lib.lqcd_kernel_variant_shape(lq.C64, n32, (ctypes.c_int * 11)()) == lq.ERR_ARG
+    piped = [sh for sh in shapes if sh["pipe"] > 0]
+    assert piped and all(sh["nrhs_fixed"] in (16, 32, 64) and sh["nr"] == 2 for sh in piped)
     assert lib.lqcd_kernel_variant_shape(lq.C64, 0, None) == lq.ERR_ARG
     # block GMRES on a batch is refused before any device work
     ctxs = (ctypes.c_void_p * 1)(h.value)
