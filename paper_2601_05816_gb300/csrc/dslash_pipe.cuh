@@ -41,18 +41,24 @@ __host__ __device__ constexpr size_t smem_bytes(int threads, int sites, bool blo
 }
 
 // One hopping direction from the shared-memory slots of this thread (st: component 0 of
-// the stage, stride `threads` float4) and of its site's link (ls: 9 complex entries).
-template <int MU, int DIR>
-__device__ __forceinline__ void hop_smem(const float4* st, int threads, const float2* ls, MC<float, 2> acc[12]) {
+// the stage, stride THREADS float4) and of its site's link (ls: 9 complex entries and the
+// padding, read as five 16-byte words).
+template <int MU, int DIR, int THREADS>
+__device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, MC<float, 2> acc[12]) {
   float2 u[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) u[e] = ls[e];
+  for (int e = 0; e < 4; ++e) {
+    const float4 q = ls[e];
+    u[2 * e] = make_float2(q.x, q.y);
+    u[2 * e + 1] = make_float2(q.z, q.w);
+  }
+  u[8] = make_float2(ls[4].x, ls[4].y);
   MC<float, 2> up[6], dn[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const float4 v = st[(size_t)k * threads];
+    const float4 v = st[k * THREADS];
     up[k].re[0] = v.x; up[k].im[0] = v.y; up[k].re[1] = v.z; up[k].im[1] = v.w;
-    const float4 w = st[(size_t)(6 + k) * threads];
+    const float4 w = st[(6 + k) * THREADS];
     dn[k].re[0] = w.x; dn[k].im[0] = w.y; dn[k].re[1] = w.z; dn[k].im[1] = w.w;
   }
   hop_compute<float, 2, MU, DIR>(u, up, dn, acc);
@@ -67,7 +73,8 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
   constexpr bool BLOCK = SELF == SELF_BLOCK || POST == POST_BLOCKINV;
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip != nullptr && *a.skip != 0) return;  // the same for every thread of the grid
-  const int threads = blockDim.x * blockDim.y, sites = blockDim.y;
+  // the launch shape is (G, MAXT / G): shared-memory offsets are compile-time constants
+  constexpr int threads = MAXT, sites = MAXT / G;
   const int lane = threadIdx.x, tid = threadIdx.y * G + lane;
   float4* sp = reinterpret_cast<float4*>(smem) + tid;
   float2* sl = reinterpret_cast<float2*>(smem + (size_t)S * 12 * threads * 16);
@@ -106,16 +113,16 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
   // copies of pipeline item `item` (directions 0..7, then the self-term input) into stage item % S
   auto issue = [&](int item) {
     if (active && item < NITEMS) {
-      float4* st = sp + (size_t)(item % S) * 12 * threads;
+      float4* st = sp + (item % S) * 12 * threads;
       const float2* src = item < 8 ? hin + (int64_t)ncb[item < 8 ? item : 0] * 12 * NRHS
                                    : a.self_in + base + (int64_t)cb * 12 * NRHS;
       src += lane * NR;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) cp16(st + (size_t)k * threads, src + k * NRHS);
+      for (int k = 0; k < 12; ++k) cp16(st + k * threads, src + k * NRHS);
       if (item < 8 && lane < kLinkSlot / 2) {
         const int it = item < 8 ? item : 0;
         const float2* lp = links + ((int64_t)(it >> 1) * a.g.V + lsite[it]) * kLinkSlot;
-        cp16(sl + ((size_t)(item % S) * sites + threadIdx.y) * kLinkSlot + 2 * lane, lp + 2 * lane);
+        cp16(sl + ((item % S) * sites + threadIdx.y) * kLinkSlot + 2 * lane, lp + 2 * lane);
       }
     }
     commit();
@@ -141,21 +148,21 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
     wait_group<S - 1>();
     __syncwarp();  // the link and block copies of the site's first lanes are visible to all its lanes
     if (active) {
-      const float4* st = sp + (size_t)(item % S) * 12 * threads;
-      const float2* ls = sl + ((size_t)(item % S) * sites + threadIdx.y) * kLinkSlot;
+      const float4* st = sp + (item % S) * 12 * threads;
+      const float4* ls = reinterpret_cast<const float4*>(sl + ((item % S) * sites + threadIdx.y) * kLinkSlot);
       switch (item) {
-        case 0: hop_smem<0, +1>(st, threads, ls, acc); break;
-        case 1: hop_smem<0, -1>(st, threads, ls, acc); break;
-        case 2: hop_smem<1, +1>(st, threads, ls, acc); break;
-        case 3: hop_smem<1, -1>(st, threads, ls, acc); break;
-        case 4: hop_smem<2, +1>(st, threads, ls, acc); break;
-        case 5: hop_smem<2, -1>(st, threads, ls, acc); break;
-        case 6: hop_smem<3, +1>(st, threads, ls, acc); break;
-        case 7: hop_smem<3, -1>(st, threads, ls, acc); break;
+        case 0: hop_smem<0, +1, threads>(st, ls, acc); break;
+        case 1: hop_smem<0, -1, threads>(st, ls, acc); break;
+        case 2: hop_smem<1, +1, threads>(st, ls, acc); break;
+        case 3: hop_smem<1, -1, threads>(st, ls, acc); break;
+        case 4: hop_smem<2, +1, threads>(st, ls, acc); break;
+        case 5: hop_smem<2, -1, threads>(st, ls, acc); break;
+        case 6: hop_smem<3, +1, threads>(st, ls, acc); break;
+        case 7: hop_smem<3, -1, threads>(st, ls, acc); break;
         default:
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
-            const float4 v = st[(size_t)k * threads];
+            const float4 v = st[k * threads];
             self[k].re[0] = v.x; self[k].im[0] = v.y; self[k].re[1] = v.z; self[k].im[1] = v.w;
           }
       }
