@@ -73,7 +73,8 @@ WORKLOADS = {
 # the summary is under profiles/). The solve's passes are the same kernel with other flags, so
 # the reported traffic per step is the timed solve's algorithmic bytes per step times this
 # ratio (FP32 basis; BF16 and other workloads: null).
-GS_DRAM_CAPTURE = {("solve", "c64", 2): (3321.96e6 + 3.17e6 + 3322.40e6 + 98.07e6 + 3321.97e6 + 97.78e6,
+GS_DRAM_CAPTURE = {("solve", "c64", 2): (3321.959424e6 + 3.148288e6 + 3322.026496e6 + 97.911552e6
+                                         + 3321.978624e6 + 97.722624e6,
                                          3 * 3321.888768e6 + 2 * 100.663296e6)}
 
 
@@ -631,6 +632,8 @@ def run_gpu(args, w):
     lat.set_gauge(U_d)
     lat.set_clover(w["m0"], w["c_sw"])
     tuning = {"c64": lat.tune(lq.C64, nrhs, reps=5), "c128": lat.tune(lq.C128, nrhs, reps=3)}
+    if args.variant >= 0:   # e.g. under a profiler, whose serialised launches distort the tuner's timings
+        lat.set_kernel_variant(lq.C64, nrhs, lq.OP_SCHUR, args.variant)
     chosen = {k: [lat.kernel_variant(d, nrhs, op) for op in (lq.OP_FULL, lq.OP_SCHUR)]
               for k, d in (("c64", lq.C64), ("c128", lq.C128))}
 
@@ -984,8 +987,9 @@ def extras_batch(args, lq, torch, line):
 def extras_gmres_large(args, lq, torch, line):
     """The 32^3 x 64 Wilson-clover workload (eps 0.25, 12 rhs, odd-even GMRES(32) to 1e-10):
     the prescribed mass m0 = -0.3 with the iteration cap --large-cap (status, iterations, true
-    residual), then the companion mass --large-m0 where the solve converges: FP32-inner mixed and
-    FP64 plain GPU time to solution and their ratio."""
+    residual), then the companion mass --large-m0 where the solve converges: FP32-inner mixed (FP32
+    storage, and the BF16 storage variant: BF16 Arnoldi basis and two-row BF16 links) and FP64 plain
+    GPU time to solution and their ratios."""
     import synthetic as syn
     wl = WORKLOADS["solve-large"]
     dims, nrhs = wl["dims"], wl["nrhs"]
@@ -1003,7 +1007,8 @@ def extras_gmres_large(args, lq, torch, line):
            "c_sw": wl["c_sw"], "solver": "odd-even GMRES(32), tol 1e-10 (true residual, per rhs)",
            "input_generation_s": t_gen}
 
-    def one(m0, precision, cap):
+    def one(m0, precision, cap, links=lq.LINKS_FP32):
+        lat.set_link_storage(links)
         lat.set_clover(m0, wl["c_sw"])
         x_d.zero_()
         torch.cuda.synchronize()
@@ -1011,9 +1016,13 @@ def extras_gmres_large(args, lq, torch, line):
         r = lat.solve(b_d, x_d, nrhs, op=lq.OP_SCHUR, precision=precision, restart_len=wl["restart"],
                       tol=wl["tol"], max_restarts=cap, use_graph=True)
         torch.cuda.synchronize()
-        return {"m0": m0, "precision": "fp32 inner / fp64 refinement" if precision == lq.C64 else "fp64",
+        secs = time.perf_counter() - t
+        name = {lq.C64: "fp32 inner / fp64 refinement", lq.BF16S: "fp32 inner arithmetic on bf16-stored basis and "
+                "two-row bf16 links / fp64 refinement"}.get(precision, "fp64")
+        lat.set_link_storage(lq.LINKS_FP32)
+        return {"m0": m0, "precision": name,
                 "status": {lq.OK: "converged", lq.NOT_CONVERGED: "not converged"}.get(r.status, str(r.status)),
-                "seconds": time.perf_counter() - t, "iterations": r.iterations, "cycles": r.restarts,
+                "seconds": secs, "iterations": r.iterations, "cycles": r.restarts,
                 "fp64_residuals": r.outer_steps, "relres_max": r.relres_max}
 
     lat.set_clover(wl["m0"], wl["c_sw"])
@@ -1022,9 +1031,11 @@ def extras_gmres_large(args, lq, torch, line):
     out["prescribed"] = one(wl["m0"], lq.C64, args.large_cap)
     out["prescribed"]["note"] = f"capped at {args.large_cap} Arnoldi cycles"
     mixed = one(args.large_m0, lq.C64, args.max_restarts)
+    mixed_bf16 = one(args.large_m0, lq.BF16S, args.max_restarts, links=lq.LINKS_BF16)
     fp64 = one(args.large_m0, lq.C128, args.max_restarts)
-    out["companion"] = {"m0": args.large_m0, "mixed": mixed, "fp64": fp64,
-                        "speedup_mixed_vs_fp64": fp64["seconds"] / mixed["seconds"]}
+    out["companion"] = {"m0": args.large_m0, "mixed": mixed, "mixed_bf16_storage": mixed_bf16, "fp64": fp64,
+                        "speedup_mixed_vs_fp64": fp64["seconds"] / mixed["seconds"],
+                        "speedup_mixed_bf16_storage_vs_fp64": fp64["seconds"] / mixed_bf16["seconds"]}
     lat.close()
     del U_d, b_d, x_d
     torch.cuda.empty_cache()
@@ -1099,7 +1110,8 @@ def main():
     ap.add_argument("--reorth", type=int, default=2, choices=[0, 1, 2],
                     help="solve workloads: Gram-Schmidt of the Arnoldi step (0 CGS1, 1 CGS2, 2 delayed CGS2)")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="apply workload: force this hopping-kernel launch variant instead of the tuned one")
+                    help="apply and solve workloads: force this FP32 hopping-kernel launch variant for the Schur "
+                         "operator instead of the tuned one")
     ap.add_argument("--no-tune", action="store_true",
                     help="apply workload with --variant: skip the autotuner (only that variant launches)")
     args = ap.parse_args()
