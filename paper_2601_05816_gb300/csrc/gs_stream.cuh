@@ -116,13 +116,14 @@ __host__ __device__ constexpr bool two_ctas(int nv, int epl) { return nv * epl <
 
 // NV: the largest nvec of the instance (8, 16, 24 or 32): the dot accumulators
 // a_i live in registers, NV * EPL complex per thread.
-// VSPLIT (update + dots, one rhs per lane, two rows per warp): the two half-warps split the
-// vectors (i even / odd) instead of the rows; each handles its vectors for both rows of the
-// warp and the update's partial sums and the updated w are exchanged with the partner lane
-// by one shuffle. Half the dot accumulators, and room for the coefficients in registers.
+// VSPLIT (dots, with or without the update; one rhs per lane, two rows per warp): the two
+// half-warps split the vectors (i even / odd) instead of the rows; each handles its vectors
+// for both rows of the warp, and the update's partial sums and the updated w are exchanged
+// with the partner lane by one shuffle. Half the dot accumulators, room for the coefficients
+// in registers, and packed FP32 (fma.rn.f32x2) for the sums.
 template <typename B, int EPL, int NV, bool UPDATE, bool DOTS, bool NORM, bool VSPLIT = false>
 __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream_kernel(const Args a) {
-  static_assert(!VSPLIT || (UPDATE && DOTS && EPL == 1 && NV % 2 == 0), "vector split: update + dots, EPL 1");
+  static_assert(!VSPLIT || (DOTS && EPL == 1 && NV % 2 == 0), "vector split: dots, EPL 1");
   using C = float2;
   if (a.skip != nullptr && *a.skip != 0) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -209,13 +210,25 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
     // with one rhs per lane the lane's update coefficients are the same for every element
     // it visits: kept in registers (one shared-memory read per basis element fewer) where
     // the instance has the registers to spare (the 16- and 32-vector ones would spill)
-    constexpr bool kCoefRegs = UPDATE && EPL == 1 && (NV == 8 || NV == 24 || VSPLIT);
+    constexpr bool kCoefRegs = UPDATE && EPL == 1 && (NV == 8 || NV == 24) && !VSPLIT;
     constexpr int NC = kCoefRegs ? NA : 1;
-    C cr[NC];  // VSPLIT: the coefficients of vectors 2k + hrow
+    C cr[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const int i = VSPLIT ? 2 * k + hrow : k;
-      cr[k] = (kCoefRegs && i < nvec && lane_on) ? cs[i * nrhs + r] : make_float2(0.f, 0.f);
+    for (int k = 0; k < NC; ++k)
+      cr[k] = (kCoefRegs && k < nvec && lane_on) ? cs[k * nrhs + r] : make_float2(0.f, 0.f);
+    // VSPLIT works on packed FP32 pairs (fma.rn.f32x2): the coefficients of vectors 2k + hrow
+    // as broadcast pairs (c.re, c.re), (c.im, c.im), and per vector the dot accumulators
+    // dp = sum (v.re w.re, v.im w.im), dq = sum (v.re w.im, -v.im w.re)
+    constexpr int NP = VSPLIT ? NA : 1;
+    C cxx[NP], cyy[NP], dp[NP], dq[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int i = 2 * k + hrow;
+      const C c = (VSPLIT && UPDATE && i < nvec && lane_on) ? cs[i * nrhs + r] : make_float2(0.f, 0.f);
+      cxx[k] = make_float2(c.x, c.x);
+      cyy[k] = make_float2(c.y, c.y);
+      dp[k] = make_float2(0.f, 0.f);
+      dq[k] = make_float2(0.f, 0.f);
     }
     // VSPLIT: the lane holding the same rhs in the other row of the warp's row pair
     const int partner = (VSPLIT && lane_on) ? (hrow == 0 ? lane + lpr : lane - lpr) : lane;
@@ -240,41 +253,44 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
           const int eA = rowA * nrhs + r, eB = eA + nrhs;
           const int e = hrow == 0 ? eA : eB;
           C wn = mine_ok ? wt[e] : make_float2(0.f, 0.f);
-          // partial update sums over this lane's vectors, for both rows (two chains each)
-          C sa[2], sb[2];
+          if constexpr (UPDATE) {
+            // partial update sums over this lane's vectors, for both rows: (sum c.re v.re, sum c.re v.im)
+            // and (sum c.im v.re, sum c.im v.im) as packed pairs
+            C xa = make_float2(0.f, 0.f), ya = xa, xb = xa, yb = xa;
 #pragma unroll
-          for (int u = 0; u < 2; ++u) { sa[u] = make_float2(0.f, 0.f); sb[u] = make_float2(0.f, 0.f); }
-#pragma unroll
-          for (int k = 0; k < NA; ++k) {
-            const int i = 2 * k + hrow;
-            if (lane_on && i < nvec) {
-              C va[1], vb[1] = {make_float2(0.f, 0.f)};
-              lds<1>(vt + (size_t)i * vte + eA, va);
-              if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
-              const C c = cr[k];
-              cmac(c, va[0], sa[k & 1]);
-              cmac(c, vb[0], sb[k & 1]);
+            for (int k = 0; k < NA; ++k) {
+              const int i = 2 * k + hrow;
+              if (lane_on && i < nvec) {
+                C va[1], vb[1] = {make_float2(0.f, 0.f)};
+                lds<1>(vt + (size_t)i * vte + eA, va);
+                if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
+                xa = __ffma2_rn(cxx[k], va[0], xa);
+                ya = __ffma2_rn(cyy[k], va[0], ya);
+                xb = __ffma2_rn(cxx[k], vb[0], xb);
+                yb = __ffma2_rn(cyy[k], vb[0], yb);
+              }
+            }
+            const C pa = make_float2(xa.x - ya.y, xa.y + ya.x);
+            const C pb = make_float2(xb.x - yb.y, xb.y + yb.x);
+            const C mine = hrow == 0 ? pa : pb, other = hrow == 0 ? pb : pa;
+            // the partner's partial for this lane's row (the partner sends its sum for the other row)
+            const float ox = __shfl_sync(0xffffffffu, other.x, partner);
+            const float oy = __shfl_sync(0xffffffffu, other.y, partner);
+            wn = make_float2(wn.x - (mine.x + ox), wn.y - (mine.y + oy));
+            if (mine_ok) {
+              const C ws[1] = {make_float2(wn.x * sc[0], wn.y * sc[0])};
+              if (a.wout != nullptr) stg<1>((B*)a.wout + row0 * nrhs + e, ws);
+              else stg<1>(w + row0 * nrhs + e, ws);
             }
           }
-          const C pa = make_float2(sa[0].x + sa[1].x, sa[0].y + sa[1].y);
-          const C pb = make_float2(sb[0].x + sb[1].x, sb[0].y + sb[1].y);
-          const C mine = hrow == 0 ? pa : pb, other = hrow == 0 ? pb : pa;
-          // the partner's partial for this lane's row (the partner sends its sum for the other row)
-          const float ox = __shfl_sync(0xffffffffu, other.x, partner);
-          const float oy = __shfl_sync(0xffffffffu, other.y, partner);
-          wn = make_float2(wn.x - (mine.x + ox), wn.y - (mine.y + oy));
-          if (mine_ok) {
-            const C ws[1] = {make_float2(wn.x * sc[0], wn.y * sc[0])};
-            if (a.wout != nullptr) stg<1>((B*)a.wout + row0 * nrhs + e, ws);
-            else stg<1>(w + row0 * nrhs + e, ws);
-            if (NORM) nn[0] = fmaf(wn.y, wn.y, fmaf(wn.x, wn.x, nn[0]));
-          }
+          if (NORM && mine_ok) nn[0] = fmaf(wn.y, wn.y, fmaf(wn.x, wn.x, nn[0]));
           // dots of this lane's vectors with the updated w of both rows
           const float wx = __shfl_sync(0xffffffffu, wn.x, partner);
           const float wy = __shfl_sync(0xffffffffu, wn.y, partner);
           C wa = hrow == 0 ? wn : make_float2(wx, wy);
           C wb = hrow == 0 ? make_float2(wx, wy) : wn;
           if (!okB) wb = make_float2(0.f, 0.f);
+          const C wa2 = make_float2(wa.y, -wa.x), wb2 = make_float2(wb.y, -wb.x);
 #pragma unroll
           for (int k = 0; k < NA; ++k) {
             const int i = 2 * k + hrow;
@@ -282,8 +298,10 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
               C va[1], vb[1] = {make_float2(0.f, 0.f)};
               lds<1>(vt + (size_t)i * vte + eA, va);
               if (okB) lds<1>(vt + (size_t)i * vte + eB, vb);
-              cdot(va[0], wa, ar[k][0], ai[k][0]);
-              cdot(vb[0], wb, ar[k][0], ai[k][0]);
+              dp[k] = __ffma2_rn(va[0], wa, dp[k]);
+              dq[k] = __ffma2_rn(va[0], wa2, dq[k]);
+              dp[k] = __ffma2_rn(vb[0], wb, dp[k]);
+              dq[k] = __ffma2_rn(vb[0], wb2, dq[k]);
             }
           }
         }
@@ -347,6 +365,13 @@ __global__ void __launch_bounds__(kThreads, two_ctas(NV, EPL) ? 2 : 1) gs_stream
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
       if (*abort_flag) break;
+    }
+    if constexpr (VSPLIT) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        ar[k][0] = dp[k].x + dp[k].y;
+        ai[k][0] = dq[k].x + dq[k].y;
+      }
     }
   }
 

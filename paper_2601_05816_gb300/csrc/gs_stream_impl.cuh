@@ -29,12 +29,14 @@ static cudaError_t launch_one(const Plan& p, int blocks, const Args& a, cudaStre
 template <typename B, int EPL, int NV>
 static cudaError_t launch_flags(bool up, bool dots, bool norm, const Plan& p, int blocks, const Args& a,
                                 cudaStream_t s) {
-  // update + dots with two rows per warp and 17-32 vectors: the vector-split consumers
+  // dots (with or without the update) with two rows per warp and 17-32 vectors: the
+  // vector-split consumers
   if constexpr (EPL == 1 && NV >= 24) {
     if (up && dots && p.H == 2) {
       if (norm) return launch_one<B, EPL, NV, true, true, true, true>(p, blocks, a, s);
       return launch_one<B, EPL, NV, true, true, false, true>(p, blocks, a, s);
     }
+    if (!up && dots && norm && p.H == 2) return launch_one<B, EPL, NV, false, true, true, true>(p, blocks, a, s);
   }
   if (up && dots && norm) return launch_one<B, EPL, NV, true, true, true>(p, blocks, a, s);
   if (!up && dots && norm) return launch_one<B, EPL, NV, false, true, true>(p, blocks, a, s);
