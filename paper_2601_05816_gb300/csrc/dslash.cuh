@@ -70,6 +70,7 @@ struct DslashArgs {
   int blk_rz;                  // > 0: blocked site mapping (ORD = 1 variants, one parity): a CTA takes the
                                // target rows (t, z0 .. z0 + blk_rz - 1, y0 .. y0 + 1); set by the launcher
   Real time_bc;                // fermion time boundary factor (+1 / -1)
+  uint64_t div_x, div_y, div_z;  // ceil(2^64 / X), ... : quotients by multiply-high (pipelined kernel; set by its launcher)
 };
 
 // NR complex numbers (NR consecutive rhs of one component).

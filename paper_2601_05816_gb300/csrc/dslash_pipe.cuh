@@ -40,11 +40,29 @@ __host__ __device__ constexpr size_t smem_bytes(int threads, int sites, bool blo
   return (size_t)S * 12 * threads * 16 + (size_t)S * sites * kLinkSlot * 8 + (block ? (size_t)sites * 72 * 4 : 0);
 }
 
-// One hopping direction from the shared-memory slots of this thread (st: component 0 of
-// the stage, stride THREADS float4) and of its site's link (ls: 9 complex entries and the
-// padding, read as five 16-byte words).
+// Complex numbers of one rhs as (re, im) register pairs: the sums of the spin projection and
+// of the reconstruction with a coefficient +1 or -1 are packed FP32 adds (add.f32x2; a - b as
+// fma.f32x2(b, -1, a), which rounds as the scalar subtraction), the +i / -i ones stay scalar.
+// a + coef * b, coef code 0: +1, 1: -1, 2: +i, 3: -i (the codes of SpinTab).
+template <int CODE>
+__device__ __forceinline__ float2 pcomb(float2 a, float2 b) {
+  if constexpr (CODE == 0) return __fadd2_rn(a, b);
+  else if constexpr (CODE == 1) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  else if constexpr (CODE == 2) return make_float2(a.x - b.y, a.y + b.x);
+  else return make_float2(a.x + b.y, a.y - b.x);
+}
+
+// One hopping direction (Sec. III-A-1: projection, SU(3) multiply, reconstruction; the same
+// operations in the same order as hop_compute) from the shared-memory slots of this thread
+// (st: component 0 of the stage, stride THREADS float4) and of its site's link (ls: 9 complex
+// entries and the padding, read as five 16-byte words), into acc[component][rhs].
 template <int MU, int DIR, int THREADS>
-__device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, MC<float, 2> acc[12]) {
+__device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, float2 acc[12][2]) {
+  using Tab = SpinTab<MU>;
+  constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);
+  constexpr int pc1 = DIR > 0 ? Tab::pc1 : neg_code(Tab::pc1);
+  constexpr int rc0 = DIR > 0 ? Tab::rc0 : neg_code(Tab::rc0);
+  constexpr int rc1 = DIR > 0 ? Tab::rc1 : neg_code(Tab::rc1);
   float2 u[9];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -53,15 +71,67 @@ __device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, MC<
     u[2 * e + 1] = make_float2(q.z, q.w);
   }
   u[8] = make_float2(ls[4].x, ls[4].y);
-  MC<float, 2> up[6], dn[6];
+  float2 up[6][2], dn[6][2];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const float4 v = st[k * THREADS];
-    up[k].re[0] = v.x; up[k].im[0] = v.y; up[k].re[1] = v.z; up[k].im[1] = v.w;
+    up[k][0] = make_float2(v.x, v.y);
+    up[k][1] = make_float2(v.z, v.w);
     const float4 w = st[(6 + k) * THREADS];
-    dn[k].re[0] = w.x; dn[k].im[0] = w.y; dn[k].re[1] = w.z; dn[k].im[1] = w.w;
+    dn[k][0] = make_float2(w.x, w.y);
+    dn[k][1] = make_float2(w.z, w.w);
   }
-  hop_compute<float, 2, MU, DIR>(u, up, dn, acc);
+  float2 h[6][2];  // [spin s][colour] of the half spinor, per rhs
+#pragma unroll
+  for (int col = 0; col < 3; ++col)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      h[col][r] = pcomb<pc0>(up[col][r], dn[3 * Tab::ps0 + col][r]);
+      h[3 + col][r] = pcomb<pc1>(up[3 + col][r], dn[3 * Tab::ps1 + col][r]);
+    }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int ar = 0; ar < 3; ++ar)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          // forward: U[ar][b] * h_b ; backward: conj(U[b][ar]) * h_b
+          const float2 m = (DIR > 0) ? u[3 * ar + b] : u[3 * b + ar];
+          const float mr = m.x, mi = (DIR > 0) ? m.y : -m.y;
+          const float2 v = h[3 * s + b][r];
+          o.x = fmaf(mr, v.x, o.x);
+          o.x = fmaf(-mi, v.y, o.x);
+          o.y = fmaf(mr, v.y, o.y);
+          o.y = fmaf(mi, v.x, o.y);
+        }
+        acc[3 * s + ar][r] = __fadd2_rn(acc[3 * s + ar][r], o);
+        // lower spin 0 takes product spin rs0, lower spin 1 product spin rs1 (a permutation)
+        if (Tab::rs0 == s) acc[6 + ar][r] = pcomb<rc0>(acc[6 + ar][r], o);
+        else acc[9 + ar][r] = pcomb<rc1>(acc[9 + ar][r], o);
+      }
+}
+
+// Quotient of a 32-bit n by d >= 2 from m = ceil(2^64 / d): floor(m n / 2^64) is exact for
+// every 32-bit n (Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019).
+__device__ __forceinline__ int fdiv(int n, uint64_t m) { return (int)__umul64hi(m, (uint64_t)(unsigned)n); }
+__host__ inline uint64_t fdiv_magic(int d) { return ~uint64_t(0) / (uint64_t)d + 1; }
+
+// site_coords (common.cuh) with the three divisions done by multiply-high.
+__device__ __forceinline__ Coord site_coords_fast(const DslashArgs<float>& a, int p, int cb) {
+  Coord c;
+  const int l2 = cb << 1;
+  const int q1 = fdiv(l2, a.div_x);
+  const int x0 = l2 - q1 * a.g.X;
+  const int q2 = fdiv(q1, a.div_y);
+  c.y = q1 - q2 * a.g.Y;
+  c.t = fdiv(q2, a.div_z);
+  c.z = q2 - c.t * a.g.Z;
+  c.x = x0 + ((p + c.t + c.z + c.y) & 1);
+  c.lex = l2 - x0 + c.x;
+  return c;
 }
 
 template <int SELF, int POST, int NRHS, int MAXT, int MINB, int S>
@@ -97,7 +167,7 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
   // neighbour cb index and link site of the eight directions (t+, t-, z+, z-, y+, y-, x+, x-)
   int ncb[8], lsite[8];
   {
-    const Coord c = site_coords(a.g, p, cb);
+    const Coord c = site_coords_fast(a, p, cb);
     const int here = eo_site, there = (1 - p) * a.g.Vh;
     ncb[0] = neighbour_lex<0, +1>(a.g, c) >> 1; lsite[0] = here;
     ncb[1] = neighbour_lex<0, -1>(a.g, c) >> 1; lsite[1] = there + ncb[1];
@@ -137,9 +207,10 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
 #pragma unroll
   for (int s = 0; s < S - 1; ++s) issue(s);
 
-  MC<float, NR> acc[12], self[12];
+  float2 accp[12][NR];
+  MC<float, NR> self[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) mc_zero(acc[k]);
+  for (int k = 0; k < 12; ++k) accp[k][0] = accp[k][1] = make_float2(0.f, 0.f);
 
 #pragma unroll
   for (int item = 0; item < NITEMS; ++item) {
@@ -151,14 +222,14 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
       const float4* st = sp + (item % S) * 12 * threads;
       const float4* ls = reinterpret_cast<const float4*>(sl + ((item % S) * sites + threadIdx.y) * kLinkSlot);
       switch (item) {
-        case 0: hop_smem<0, +1, threads>(st, ls, acc); break;
-        case 1: hop_smem<0, -1, threads>(st, ls, acc); break;
-        case 2: hop_smem<1, +1, threads>(st, ls, acc); break;
-        case 3: hop_smem<1, -1, threads>(st, ls, acc); break;
-        case 4: hop_smem<2, +1, threads>(st, ls, acc); break;
-        case 5: hop_smem<2, -1, threads>(st, ls, acc); break;
-        case 6: hop_smem<3, +1, threads>(st, ls, acc); break;
-        case 7: hop_smem<3, -1, threads>(st, ls, acc); break;
+        case 0: hop_smem<0, +1, threads>(st, ls, accp); break;
+        case 1: hop_smem<0, -1, threads>(st, ls, accp); break;
+        case 2: hop_smem<1, +1, threads>(st, ls, accp); break;
+        case 3: hop_smem<1, -1, threads>(st, ls, accp); break;
+        case 4: hop_smem<2, +1, threads>(st, ls, accp); break;
+        case 5: hop_smem<2, -1, threads>(st, ls, accp); break;
+        case 6: hop_smem<3, +1, threads>(st, ls, accp); break;
+        case 7: hop_smem<3, -1, threads>(st, ls, accp); break;
         default:
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
@@ -171,10 +242,16 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
   wait_group<0>();
   if (!active) return;
 
+  MC<float, NR> acc[12];
+  const float2 ch = make_float2(a.c_hop, a.c_hop);
 #pragma unroll
   for (int k = 0; k < 12; ++k)
 #pragma unroll
-    for (int q = 0; q < NR; ++q) { acc[k].re[q] *= a.c_hop; acc[k].im[q] *= a.c_hop; }
+    for (int q = 0; q < NR; ++q) {
+      const float2 v = __fmul2_rn(accp[k][q], ch);
+      acc[k].re[q] = v.x;
+      acc[k].im[q] = v.y;
+    }
   const float* bl = sb + threadIdx.y * 72;
   if (SELF == SELF_SCALAR) {
 #pragma unroll
@@ -224,7 +301,11 @@ cudaError_t launch_pipe_one(const DslashArgs<float>& a, cudaStream_t stream) {
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   });
   const dim3 grid((a.n_target + block.y - 1) / block.y);
-  kern<<<grid, block, smem, stream>>>(a);
+  DslashArgs<float> b = a;
+  b.div_x = fdiv_magic(a.g.X);
+  b.div_y = fdiv_magic(a.g.Y);
+  b.div_z = fdiv_magic(a.g.Z);
+  kern<<<grid, block, smem, stream>>>(b);
   return cudaGetLastError();
 }
 
