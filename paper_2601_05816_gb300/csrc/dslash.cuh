@@ -24,6 +24,7 @@
 // from L1/L2: each spinor is used by its eight neighbours, which the lexicographic
 // thread order keeps within a few time slices, well inside the 129 MB L2.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -188,12 +189,90 @@ template <> struct SpinTab<3> { enum { ps0 = 1, pc0 = 3, ps1 = 0, pc1 = 3, rs0 =
 
 __host__ __device__ constexpr int neg_code(int c) { return c == 0 ? 1 : c == 1 ? 0 : c == 2 ? 3 : 2; }
 
+// Complex numbers of one rhs as (re, im) register pairs: the sums of the spin projection and
+// of the reconstruction with a coefficient +1 or -1 are packed FP32 adds (add.f32x2; a - b as
+// fma.f32x2(b, -1, a), which rounds as the scalar subtraction), the +i / -i ones stay scalar.
+// a + coef * b, coef code 0: +1, 1: -1, 2: +i, 3: -i (the codes of SpinTab).
+template <int CODE>
+__device__ __forceinline__ float2 pcomb(float2 a, float2 b) {
+  if constexpr (CODE == 0) return __fadd2_rn(a, b);
+  else if constexpr (CODE == 1) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  else if constexpr (CODE == 2) return make_float2(a.x - b.y, a.y + b.x);
+  else return make_float2(a.x + b.y, a.y - b.x);
+}
+
+// The direction of hop_compute below for FP32 and two rhs per thread, on (re, im) pairs: the
+// same operations in the same order, the +-1 sums packed.
+template <int MU, int DIR>
+__device__ __forceinline__ void hop_compute_pairs(const float2* u, const float2 (*up)[2], const float2 (*dn)[2],
+                                                  float2 (*acc)[2]) {
+  using Tab = SpinTab<MU>;
+  constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);
+  constexpr int pc1 = DIR > 0 ? Tab::pc1 : neg_code(Tab::pc1);
+  constexpr int rc0 = DIR > 0 ? Tab::rc0 : neg_code(Tab::rc0);
+  constexpr int rc1 = DIR > 0 ? Tab::rc1 : neg_code(Tab::rc1);
+  float2 h[6][2];  // [spin s][colour] of the half spinor, per rhs
+#pragma unroll
+  for (int col = 0; col < 3; ++col)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      h[col][r] = pcomb<pc0>(up[col][r], dn[3 * Tab::ps0 + col][r]);
+      h[3 + col][r] = pcomb<pc1>(up[3 + col][r], dn[3 * Tab::ps1 + col][r]);
+    }
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int ar = 0; ar < 3; ++ar)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          // forward: U[ar][b] * h_b ; backward: conj(U[b][ar]) * h_b
+          const float2 m = (DIR > 0) ? u[3 * ar + b] : u[3 * b + ar];
+          const float mr = m.x, mi = (DIR > 0) ? m.y : -m.y;
+          const float2 v = h[3 * s + b][r];
+          o.x = fmaf(mr, v.x, o.x);
+          o.x = fmaf(-mi, v.y, o.x);
+          o.y = fmaf(mr, v.y, o.y);
+          o.y = fmaf(mi, v.x, o.y);
+        }
+        acc[3 * s + ar][r] = __fadd2_rn(acc[3 * s + ar][r], o);
+        // lower spin 0 takes product spin rs0, lower spin 1 product spin rs1 (a permutation)
+        if (Tab::rs0 == s) acc[6 + ar][r] = pcomb<rc0>(acc[6 + ar][r], o);
+        else acc[9 + ar][r] = pcomb<rc1>(acc[9 + ar][r], o);
+      }
+}
+
 // Spin projection, SU(3) multiply and reconstruction of one hopping direction
 // (forward for DIR = +1, backward for DIR = -1) from the neighbour spinor (upper
 // spins up[6], lower spins dn[6]) and the link u[9] (row-major).
 template <typename Real, int NR, int MU, int DIR>
 __device__ __forceinline__ void hop_compute(const typename Cplx<Real>::T* u, const MC<Real, NR>* up,
                                             const MC<Real, NR>* dn, MC<Real, NR> acc[12]) {
+  if constexpr (std::is_same<Real, float>::value && NR == 2) {
+    float2 upp[6][2], dnp[6][2], accp[12][2];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        upp[k][r] = make_float2(up[k].re[r], up[k].im[r]);
+        dnp[k][r] = make_float2(dn[k].re[r], dn[k].im[r]);
+      }
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) accp[k][r] = make_float2(acc[k].re[r], acc[k].im[r]);
+    hop_compute_pairs<MU, DIR>(u, upp, dnp, accp);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        acc[k].re[r] = accp[k][r].x;
+        acc[k].im[r] = accp[k][r].y;
+      }
+    return;
+  }
   using C = typename Cplx<Real>::T;
   using Tab = SpinTab<MU>;
   constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);

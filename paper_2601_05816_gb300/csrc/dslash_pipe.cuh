@@ -40,29 +40,12 @@ __host__ __device__ constexpr size_t smem_bytes(int threads, int sites, bool blo
   return (size_t)S * 12 * threads * 16 + (size_t)S * sites * kLinkSlot * 8 + (block ? (size_t)sites * 72 * 4 : 0);
 }
 
-// Complex numbers of one rhs as (re, im) register pairs: the sums of the spin projection and
-// of the reconstruction with a coefficient +1 or -1 are packed FP32 adds (add.f32x2; a - b as
-// fma.f32x2(b, -1, a), which rounds as the scalar subtraction), the +i / -i ones stay scalar.
-// a + coef * b, coef code 0: +1, 1: -1, 2: +i, 3: -i (the codes of SpinTab).
-template <int CODE>
-__device__ __forceinline__ float2 pcomb(float2 a, float2 b) {
-  if constexpr (CODE == 0) return __fadd2_rn(a, b);
-  else if constexpr (CODE == 1) return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-  else if constexpr (CODE == 2) return make_float2(a.x - b.y, a.y + b.x);
-  else return make_float2(a.x + b.y, a.y - b.x);
-}
-
-// One hopping direction (Sec. III-A-1: projection, SU(3) multiply, reconstruction; the same
-// operations in the same order as hop_compute) from the shared-memory slots of this thread
+// One hopping direction (Sec. III-A-1: projection, SU(3) multiply, reconstruction, on (re, im)
+// pairs: hop_compute_pairs) from the shared-memory slots of this thread
 // (st: component 0 of the stage, stride THREADS float4) and of its site's link (ls: 9 complex
 // entries and the padding, read as five 16-byte words), into acc[component][rhs].
 template <int MU, int DIR, int THREADS>
 __device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, float2 acc[12][2]) {
-  using Tab = SpinTab<MU>;
-  constexpr int pc0 = DIR > 0 ? Tab::pc0 : neg_code(Tab::pc0);
-  constexpr int pc1 = DIR > 0 ? Tab::pc1 : neg_code(Tab::pc1);
-  constexpr int rc0 = DIR > 0 ? Tab::rc0 : neg_code(Tab::rc0);
-  constexpr int rc1 = DIR > 0 ? Tab::rc1 : neg_code(Tab::rc1);
   float2 u[9];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -81,37 +64,7 @@ __device__ __forceinline__ void hop_smem(const float4* st, const float4* ls, flo
     dn[k][0] = make_float2(w.x, w.y);
     dn[k][1] = make_float2(w.z, w.w);
   }
-  float2 h[6][2];  // [spin s][colour] of the half spinor, per rhs
-#pragma unroll
-  for (int col = 0; col < 3; ++col)
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      h[col][r] = pcomb<pc0>(up[col][r], dn[3 * Tab::ps0 + col][r]);
-      h[3 + col][r] = pcomb<pc1>(up[3 + col][r], dn[3 * Tab::ps1 + col][r]);
-    }
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int ar = 0; ar < 3; ++ar)
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        float2 o = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          // forward: U[ar][b] * h_b ; backward: conj(U[b][ar]) * h_b
-          const float2 m = (DIR > 0) ? u[3 * ar + b] : u[3 * b + ar];
-          const float mr = m.x, mi = (DIR > 0) ? m.y : -m.y;
-          const float2 v = h[3 * s + b][r];
-          o.x = fmaf(mr, v.x, o.x);
-          o.x = fmaf(-mi, v.y, o.x);
-          o.y = fmaf(mr, v.y, o.y);
-          o.y = fmaf(mi, v.x, o.y);
-        }
-        acc[3 * s + ar][r] = __fadd2_rn(acc[3 * s + ar][r], o);
-        // lower spin 0 takes product spin rs0, lower spin 1 product spin rs1 (a permutation)
-        if (Tab::rs0 == s) acc[6 + ar][r] = pcomb<rc0>(acc[6 + ar][r], o);
-        else acc[9 + ar][r] = pcomb<rc1>(acc[9 + ar][r], o);
-      }
+  hop_compute_pairs<MU, DIR>(u, up, dn, acc);
 }
 
 // Quotient of a 32-bit n by d >= 2 from m = ceil(2^64 / d): floor(m n / 2^64) is exact for
@@ -242,37 +195,35 @@ __global__ void __launch_bounds__(MAXT, MINB) dslash_pipe_kernel(DslashArgs<floa
   wait_group<0>();
   if (!active) return;
 
+  // scale the hopping sum by c_hop and add the self term: for A psi (pass B) one packed FMA
+  // per complex number, c_hop * hop + (A psi)
   MC<float, NR> acc[12];
   const float2 ch = make_float2(a.c_hop, a.c_hop);
+  const float* bl = sb + threadIdx.y * 72;
+  MC<float, NR> t[12];
+  if (SELF == SELF_BLOCK) {
+    block_matvec<float, NR>(bl, self, t);
+    block_matvec<float, NR>(bl + 36, self + 6, t + 6);
+  }
 #pragma unroll
   for (int k = 0; k < 12; ++k)
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-      const float2 v = __fmul2_rn(accp[k][q], ch);
+      float2 v;
+      if (SELF == SELF_BLOCK) {
+        v = __ffma2_rn(accp[k][q], ch, make_float2(t[k].re[q], t[k].im[q]));
+      } else {
+        v = __fmul2_rn(accp[k][q], ch);
+        if (SELF == SELF_SCALAR) {
+          const float2 ss = make_float2(a.self_scalar, a.self_scalar);
+          v = __ffma2_rn(ss, make_float2(self[k].re[q], self[k].im[q]), v);
+        }
+      }
       acc[k].re[q] = v.x;
       acc[k].im[q] = v.y;
     }
-  const float* bl = sb + threadIdx.y * 72;
-  if (SELF == SELF_SCALAR) {
-#pragma unroll
-    for (int k = 0; k < 12; ++k)
-#pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        acc[k].re[q] = fmaf(a.self_scalar, self[k].re[q], acc[k].re[q]);
-        acc[k].im[q] = fmaf(a.self_scalar, self[k].im[q], acc[k].im[q]);
-      }
-  } else if (SELF == SELF_BLOCK) {
-    MC<float, NR> t[12];
-    block_matvec<float, NR>(bl, self, t);
-    block_matvec<float, NR>(bl + 36, self + 6, t + 6);
-#pragma unroll
-    for (int k = 0; k < 12; ++k)
-#pragma unroll
-      for (int q = 0; q < NR; ++q) { acc[k].re[q] += t[k].re[q]; acc[k].im[q] += t[k].im[q]; }
-  }
   float2* op = a.out + base + (int64_t)cb * 12 * NRHS + lane * NR;
   if (POST == POST_BLOCKINV) {
-    MC<float, NR> t[12];
     block_matvec<float, NR>(bl, acc, t);
     block_matvec<float, NR>(bl + 36, acc + 6, t + 6);
 #pragma unroll
