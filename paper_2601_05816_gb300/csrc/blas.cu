@@ -707,7 +707,7 @@ cudaError_t launch_scale_inplace(bool f64, int64_t n, int nrhs, void* v, const d
 // correction of one restart cycle; its rounding is removed by the next FP64
 // true residual) and added to x in FP64. A CTA owns tiles of EPT * blockDim.x
 // consecutive elements and walks the vectors in the outer loop: per vector it reads
-// one contiguous run of the tile (EPT independent loads in flight per thread), with
+// one contiguous run of the tile (four vectors at a time: 4 EPT independent loads in flight per thread), with
 // the partial sums of its EPT elements in registers. blockDim.x is a multiple of
 // nrhs, so a thread's rhs (and its coefficients) are the same for all its elements.
 template <typename C, typename B, int EPT>
@@ -726,7 +726,30 @@ update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstrid
     Real sr[EPT], si[EPT];
 #pragma unroll
     for (int u = 0; u < EPT; ++u) { sr[u] = 0; si[u] = 0; }
-    for (int i = 0; i < k; ++i) {
+    // four vectors per step: their EPT loads each are independent, so 4 EPT are in flight
+    int i = 0;
+    for (; i + 4 <= k; i += 4) {
+      C v[4][EPT];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const B* vi = basis + (i + q) * vstride + base + threadIdx.x;
+#pragma unroll
+        for (int u = 0; u < EPT; ++u)
+          v[q][u] = base + threadIdx.x + (int64_t)u * blockDim.x < n ? C(ld_basis(vi + (int64_t)u * blockDim.x))
+                                                                      : C{};
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double2 c = ys[(i + q) * nrhs + r];
+        const Real crr = (Real)c.x, cii = (Real)c.y;
+#pragma unroll
+        for (int u = 0; u < EPT; ++u) {
+          sr[u] += crr * v[q][u].x - cii * v[q][u].y;
+          si[u] += crr * v[q][u].y + cii * v[q][u].x;
+        }
+      }
+    }
+    for (; i < k; ++i) {
       const double2 c = ys[i * nrhs + r];
       const Real crr = (Real)c.x, cii = (Real)c.y;
       const B* vi = basis + i * vstride + base + threadIdx.x;
@@ -755,7 +778,7 @@ update_x_kernel(int64_t n, int nrhs, const B* __restrict__ basis, int64_t vstrid
 cudaError_t launch_update_x(bool basis_f64, int64_t n, int nrhs, int nvec_max, const void* basis,
                             int64_t vstride, const void* y, const int* kmax, void* x,
                             cudaStream_t stream, bool basis_bf16) {
-  constexpr int EPT = 8;
+  constexpr int EPT = 4;
   const int threads = nrhs * (256 / nrhs);
   int64_t tiles = (n + (int64_t)threads * EPT - 1) / ((int64_t)threads * EPT);
   const int blocks = (int)(tiles < 1 ? 1 : (tiles > 152 * 8 ? 152 * 8 : tiles));
